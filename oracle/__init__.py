@@ -1,0 +1,11 @@
+"""CPU FP64 oracle for FLAPW H/S assembly.
+
+TEST INFRASTRUCTURE: only tests, the smoke check and the CPU-baseline leg of
+the benchmark may import this package.  It shares no code with the CUDA
+library, and the library never calls it.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
+(exact brute force, closed forms, invariants, textbook Cholesky checks).
+"""
+from .hs_oracle import assemble, h_aa, rel_frobenius  # noqa: F401
+from .cholesky import cholesky_lower, fail_flags  # noqa: F401

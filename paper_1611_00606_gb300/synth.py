@@ -1,0 +1,163 @@
+"""Seeded synthetic inputs for FLAPW H/S assembly (shared by the oracle tests,
+the GPU tests, ``smoke()`` and ``bench.py``).
+
+This module holds no arithmetic of the method itself: it only draws the
+coefficient blocks A, B, the per-atom T matrices and the U norms with the
+shapes and structure of Sec. 2 (matrix sizes after Eq. (s); N_L = (l_max+1)^2
+and N_G ranges of Tab. 1) and of the Hermitian / positive-definite facts stated
+for S, H and T in Sec. 1.1.  The physical inputs (NaCl, AuAg from FLEUR) are
+not available, so these draws stand in for them.
+
+Recipe (one tensor id per array, ``numpy.random.Philox(key=(seed, id))``):
+
+* complex normal ``z = (x + i y)`` with ``x, y ~ N(0, 1/2)`` (so E|z|^2 = 1);
+* ``A_a``, ``B_a``: complex normal, row ``L`` (0-based inside the atom)
+  scaled by ``1 / (1 + floor(sqrt(L)))`` -- the angular-momentum ``l`` of
+  the compound index ``L = (l, m)``;
+* ``T_AA[a] = M M^H + N_L I`` (HPD, smallest eigenvalue >= N_L), except the
+  "indefinite" atoms where the diagonal is shifted by ``-2 N_L``;
+* ``T_AB[a]``: complex normal; ``T_BB[a] = (N + N^H) / 2``;
+* every Hermitian draw is symmetrised exactly, ``T <- (T + T^H) / 2``;
+* ``U[a, L]``: uniform in [0.5, 2].
+
+Indefinite atoms: ``n_f = round(frac * N_A)`` atoms at
+``(3 + floor(i * N_A / n_f)) mod N_A`` for ``i < n_f``.
+
+Memory layout (identical to the C ABI, BLAS column-major):
+
+* ``A``, ``B``: numpy arrays of shape ``(K, N_G)``, ``K = N_A * N_L``,
+  Fortran order (each column of length K is contiguous; atom ``a`` owns
+  rows ``[a*N_L, (a+1)*N_L)``);
+* ``T_AA``, ``T_AB``, ``T_BB``: shape ``(N_A, N_L, N_L)`` in natural math
+  orientation (``T[a][r, c]``); ``as_colmajor_T`` gives the ABI order;
+* ``U``: shape ``(N_A, N_L)`` float64, C order.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# tensor ids of the counter-based streams
+_ID_A, _ID_B, _ID_TAA, _ID_TAB, _ID_TBB, _ID_U = 1, 2, 3, 4, 5, 6
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """One k-point assembly problem: sizes plus the indefinite-atom fraction."""
+    name: str
+    N_A: int
+    N_L: int
+    N_G: int
+    indefinite: tuple  # 0-based atom indices whose T_AA is indefinite
+    seed: int = 0
+
+    @property
+    def K(self) -> int:
+        return self.N_A * self.N_L
+
+
+def indefinite_atoms(N_A: int, frac: float) -> tuple:
+    """Atoms given an indefinite T_AA: n_f = round(frac*N_A), spread from atom 3."""
+    n_f = int(round(frac * N_A))
+    if n_f <= 0:
+        return ()
+    return tuple(sorted({(3 + (i * N_A) // n_f) % N_A for i in range(n_f)}))
+
+
+# The five problem shapes.  "tiny" is small enough for the oracle in a second;
+# the paper-scale shapes follow Tab. 1 (N_L = 121 = (10+1)^2 as AuAg,
+# N_G in the K_max range) and the sizes stated after Eq. (s).
+WORKLOADS = {
+    "tiny": Workload("tiny", 4, 16, 256, (3,)),
+    "auag_like_4000": Workload("auag_like_4000", 100, 121, 4000, indefinite_atoms(100, 0.05)),
+    "large_12000": Workload("large_12000", 256, 144, 12000, indefinite_atoms(256, 0.02)),
+    "split_8000": Workload("split_8000", 100, 121, 8000, indefinite_atoms(100, 0.05)),
+}
+
+
+def _rng(seed: int, tid: int, sub: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=[seed, tid * 1_000_003 + sub]))
+
+
+def _cnormal(rng: np.random.Generator, shape) -> np.ndarray:
+    x = rng.standard_normal(size=(2,) + tuple(shape))
+    s = math.sqrt(0.5)
+    return (x[0] * s) + 1j * (x[1] * s)
+
+
+def _herm(T: np.ndarray) -> np.ndarray:
+    """Exact Hermitian symmetrisation (T + T^H)/2 on the last two axes."""
+    return 0.5 * (T + np.conj(np.swapaxes(T, -1, -2)))
+
+
+def l_of_L(N_L: int) -> np.ndarray:
+    """Angular momentum l of each compound row index L = l^2 + l + m (0-based)."""
+    return np.floor(np.sqrt(np.arange(N_L))).astype(np.int64)
+
+
+def coefficients(N_A: int, N_L: int, N_G: int, seed: int = 0, tid: int = _ID_A,
+                 col0: int = 0, chunk: int = 512) -> np.ndarray:
+    """A complex (K, N_G) Fortran-order coefficient matrix (A or B).
+
+    Columns are drawn in independent chunks of ``chunk`` columns (one Philox
+    stream per chunk) so any column range can be regenerated on its own;
+    ``col0`` is the global index of the first returned column.
+    """
+    K = N_A * N_L
+    scale = 1.0 / (1.0 + l_of_L(N_L).astype(np.float64))
+    rowscale = np.tile(scale, N_A)  # (K,)
+    out = np.empty((N_G, K), dtype=np.complex128)  # C order: row g = column g
+    g = 0
+    while g < N_G:
+        gg = col0 + g
+        c = gg // chunk
+        lo = gg - c * chunk
+        n = min(chunk - lo, N_G - g)
+        blk = _cnormal(_rng(seed, tid, c), (chunk, K))[lo:lo + n]
+        out[g:g + n] = blk * rowscale[None, :]
+        g += n
+    return out.T  # (K, N_G), Fortran order
+
+
+def t_matrices(N_A: int, N_L: int, indefinite=(), seed: int = 0):
+    """(T_AA, T_AB, T_BB), each (N_A, N_L, N_L) complex128, natural orientation."""
+    M = _cnormal(_rng(seed, _ID_TAA), (N_A, N_L, N_L))
+    T_AA = M @ np.conj(np.swapaxes(M, -1, -2))
+    eye = np.eye(N_L)
+    T_AA = T_AA + N_L * eye[None]
+    for a in indefinite:
+        T_AA[a] -= 2 * N_L * eye
+    T_AA = _herm(T_AA)
+    T_AB = _cnormal(_rng(seed, _ID_TAB), (N_A, N_L, N_L))
+    N = _cnormal(_rng(seed, _ID_TBB), (N_A, N_L, N_L))
+    T_BB = _herm(N)
+    return T_AA, T_AB, T_BB
+
+
+def u_norms(N_A: int, N_L: int, seed: int = 0) -> np.ndarray:
+    return _rng(seed, _ID_U).uniform(0.5, 2.0, size=(N_A, N_L))
+
+
+def make_inputs(w: Workload, cols: slice | None = None):
+    """Draw every input of workload ``w``.
+
+    Returns dict with A, B (K, N_G or the requested column range), T_AA, T_AB,
+    T_BB (N_A, N_L, N_L) and U (N_A, N_L).
+    """
+    if cols is None:
+        c0, n = 0, w.N_G
+    else:
+        c0, c1, _ = cols.indices(w.N_G)
+        n = c1 - c0
+    A = coefficients(w.N_A, w.N_L, n, w.seed, _ID_A, col0=c0)
+    B = coefficients(w.N_A, w.N_L, n, w.seed, _ID_B, col0=c0)
+    T_AA, T_AB, T_BB = t_matrices(w.N_A, w.N_L, w.indefinite, w.seed)
+    U = u_norms(w.N_A, w.N_L, w.seed)
+    return dict(A=A, B=B, T_AA=T_AA, T_AB=T_AB, T_BB=T_BB, U=U)
+
+
+def as_colmajor_T(T: np.ndarray) -> np.ndarray:
+    """(N_A, N_L, N_L) natural -> C-contiguous buffer holding each T_a column-major."""
+    return np.ascontiguousarray(np.swapaxes(T, -1, -2))

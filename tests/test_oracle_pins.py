@@ -1,0 +1,206 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+No GPU.  Each test is chosen so that a plausible slip in the oracle (a dropped
+term of Eq. (h)/(s), T^BA not conjugate-transposed, U applied once instead of
+squared, a wrong atom-row offset, a transposed operand) fails at least one:
+
+* exact rational brute force of the index forms (Sec. 1.1) on tiny inputs;
+* closed forms: T = I gives H = (A+B)^H (A+B); S = C^H C with C the
+  row-stacked [A; U B] (Sec. 2's stacking argument);
+* invariants: H and S Hermitian (Sec. 1.1); rank(S) = min(N_G, 2 N_A N_L)
+  and S positive definite when 2 N_A N_L >= N_G; atom-permutation
+  invariance; column-permutation equivariance; linearity in T;
+* the textbook Cholesky against LAPACK (numpy) and its failure semantics.
+"""
+import numpy as np
+import pytest
+
+from oracle import assemble, h_aa, rel_frobenius, cholesky_lower, fail_flags
+from oracle import brute
+from paper_1611_00606_gb300 import synth
+
+EPS = np.finfo(np.float64).eps
+
+
+def _inputs(N_A, N_L, N_G, indefinite=(), seed=0):
+    w = synth.Workload("t", N_A, N_L, N_G, tuple(indefinite), seed)
+    return synth.make_inputs(w)
+
+
+def _run(d, N_A, N_L, **kw):
+    return assemble(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], N_A, N_L, **kw)
+
+
+@pytest.mark.parametrize("N_A,N_L,N_G,indef", [(1, 1, 1, ()), (2, 4, 5, (1,)), (3, 4, 8, (0,))])
+def test_exact_brute_force(N_A, N_L, N_G, indef):
+    d = _inputs(N_A, N_L, N_G, indef, seed=7)
+    H, S = _run(d, N_A, N_L)
+    He, Se = brute.exact_hs(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], N_A, N_L)
+    He, Se = brute.to_complex(He), brute.to_complex(Se)
+    Hb, Sb = brute.abs_sum_bound(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], N_A, N_L)
+    # standard dot-product rounding bound, n = number of summed products
+    n = 4 * N_A * N_L * N_L + 8
+    assert np.all(np.abs(H - He) <= n * EPS * Hb + 1e-300)
+    assert np.all(np.abs(S - Se) <= n * EPS * Sb + 1e-300)
+
+
+def test_brute_force_detects_transposed_tba():
+    """A reading that forgets the conjugate transpose of T^AB is far from exact."""
+    N_A, N_L, N_G = 2, 4, 5
+    d = _inputs(N_A, N_L, N_G, seed=3)
+    He, _ = brute.exact_hs(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], N_A, N_L)
+    He = brute.to_complex(He)
+    wrong = np.zeros_like(He)
+    for a in range(N_A):
+        r = slice(a * N_L, (a + 1) * N_L)
+        Aa, Ba = d["A"][r], d["B"][r]
+        wrong += Aa.conj().T @ d["T_AA"][a] @ Aa + Aa.conj().T @ d["T_AB"][a] @ Ba
+        wrong += Ba.conj().T @ d["T_AB"][a] @ Aa + Ba.conj().T @ d["T_BB"][a] @ Ba
+    assert rel_frobenius(wrong, He) > 1e-3
+
+
+def test_identity_T_closed_form():
+    N_A, N_L, N_G = 3, 9, 40
+    d = _inputs(N_A, N_L, N_G, seed=1)
+    I = np.broadcast_to(np.eye(N_L, dtype=np.complex128), (N_A, N_L, N_L)).copy()
+    ones = np.ones((N_A, N_L))
+    H, S = assemble(d["A"], d["B"], I, I, I, ones, N_A, N_L)
+    C = d["A"] + d["B"]
+    assert rel_frobenius(H, C.conj().T @ C) < 1e-14
+    St = np.vstack([d["A"], d["B"]])
+    assert rel_frobenius(S, St.conj().T @ St) < 1e-14
+
+
+def test_overlap_stacked_closed_form():
+    N_A, N_L, N_G = 4, 16, 64
+    d = _inputs(N_A, N_L, N_G, seed=2)
+    _, S = _run(d, N_A, N_L)
+    C = np.vstack([d["A"], d["U"].reshape(-1)[:, None] * d["B"]])
+    assert rel_frobenius(S, C.conj().T @ C) < 1e-14
+
+
+def test_haa_identity_equals_overlap_of_A():
+    """B = 0, T^AA = I: H = A^H A = S."""
+    N_A, N_L, N_G = 3, 16, 50
+    d = _inputs(N_A, N_L, N_G, seed=4)
+    Z = np.zeros_like(d["B"])
+    I = np.broadcast_to(np.eye(N_L, dtype=np.complex128), (N_A, N_L, N_L)).copy()
+    H, S = assemble(d["A"], Z, I, d["T_AB"], d["T_BB"], d["U"], N_A, N_L)
+    assert rel_frobenius(H, S) < 1e-14
+    assert rel_frobenius(h_aa(d["A"], I, N_A, N_L), S) < 1e-14
+
+
+def test_hermitian():
+    N_A, N_L, N_G = 4, 16, 256
+    d = _inputs(N_A, N_L, N_G, (3,), seed=0)
+    H, S = _run(d, N_A, N_L)
+    assert rel_frobenius(H, H.conj().T) < 1e-14
+    assert rel_frobenius(S, S.conj().T) < 1e-14
+
+
+def test_overlap_rank_deficient_tiny():
+    """tiny shape: 2 N_A N_L = 128 < N_G = 256, so S is PSD with rank 128."""
+    w = synth.WORKLOADS["tiny"]
+    d = synth.make_inputs(w)
+    _, S = _run(d, w.N_A, w.N_L)
+    ev = np.linalg.eigvalsh(0.5 * (S + S.conj().T))
+    top = ev.max()
+    r = 2 * w.N_A * w.N_L
+    assert np.all(np.abs(ev[: w.N_G - r]) < 1e-12 * top)
+    assert ev[w.N_G - r] > 1e-6 * top
+
+
+def test_overlap_positive_definite_when_full_rank():
+    N_A, N_L, N_G = 4, 16, 100  # 2 N_A N_L = 128 >= 100
+    d = _inputs(N_A, N_L, N_G, seed=5)
+    _, S = _run(d, N_A, N_L)
+    np.linalg.cholesky(0.5 * (S + S.conj().T))  # raises if not PD
+    assert np.linalg.eigvalsh(0.5 * (S + S.conj().T)).min() > 0
+
+
+def test_atom_permutation_invariance():
+    N_A, N_L, N_G = 4, 9, 30
+    d = _inputs(N_A, N_L, N_G, (2,), seed=6)
+    H, S = _run(d, N_A, N_L)
+    perm = np.array([2, 0, 3, 1])
+    rows = np.concatenate([np.arange(a * N_L, (a + 1) * N_L) for a in perm])
+    dp = dict(A=d["A"][rows], B=d["B"][rows], T_AA=d["T_AA"][perm], T_AB=d["T_AB"][perm],
+              T_BB=d["T_BB"][perm], U=d["U"][perm])
+    Hp, Sp = _run(dp, N_A, N_L)
+    assert rel_frobenius(Hp, H) < 1e-14 and rel_frobenius(Sp, S) < 1e-14
+
+
+def test_column_permutation_equivariance():
+    N_A, N_L, N_G = 3, 9, 30
+    d = _inputs(N_A, N_L, N_G, seed=8)
+    H, S = _run(d, N_A, N_L)
+    p = np.random.default_rng(0).permutation(N_G)
+    dp = dict(d, A=d["A"][:, p], B=d["B"][:, p])
+    Hp, Sp = _run(dp, N_A, N_L)
+    assert rel_frobenius(Hp, H[np.ix_(p, p)]) < 1e-14
+    assert rel_frobenius(Sp, S[np.ix_(p, p)]) < 1e-14
+
+
+def test_linearity_in_T():
+    N_A, N_L, N_G = 2, 9, 20
+    d1 = _inputs(N_A, N_L, N_G, seed=9)
+    d2 = _inputs(N_A, N_L, N_G, seed=10)
+    dsum = dict(d1, T_AA=d1["T_AA"] + d2["T_AA"], T_AB=d1["T_AB"] + d2["T_AB"],
+                T_BB=d1["T_BB"] + d2["T_BB"])
+    d2b = dict(d1, T_AA=d2["T_AA"], T_AB=d2["T_AB"], T_BB=d2["T_BB"])
+    H1, _ = _run(d1, N_A, N_L)
+    H2, _ = _run(d2b, N_A, N_L)
+    Hs, _ = _run(dsum, N_A, N_L)
+    assert rel_frobenius(Hs, H1 + H2) < 1e-14
+
+
+def test_single_column_is_real():
+    N_A, N_L = 3, 16
+    d = _inputs(N_A, N_L, 1, seed=11)
+    H, S = _run(d, N_A, N_L)
+    assert abs(H[0, 0].imag) <= 1e-14 * abs(H[0, 0])
+    assert abs(S[0, 0].imag) <= 1e-14 * abs(S[0, 0]) and S[0, 0].real > 0
+
+
+def test_column_panel_matches_full():
+    N_A, N_L, N_G = 3, 9, 40
+    d = _inputs(N_A, N_L, N_G, (1,), seed=12)
+    H, S = _run(d, N_A, N_L)
+    cols = np.array([0, 7, 39])
+    Hp, Sp = _run(d, N_A, N_L, cols=cols)
+    assert np.array_equal(Hp.shape, (N_G, 3))
+    assert rel_frobenius(Hp, H[:, cols]) < 1e-15 and rel_frobenius(Sp, S[:, cols]) < 1e-15
+
+
+def test_cholesky_matches_lapack_and_flags():
+    w = synth.WORKLOADS["tiny"]
+    d = synth.make_inputs(w)
+    for a in range(w.N_A):
+        L, ok = cholesky_lower(d["T_AA"][a])
+        if a in w.indefinite:
+            assert not ok
+            with pytest.raises(np.linalg.LinAlgError):
+                np.linalg.cholesky(d["T_AA"][a])
+        else:
+            assert ok
+            assert rel_frobenius(L @ L.conj().T, d["T_AA"][a]) < 1e-14
+            assert rel_frobenius(L, np.linalg.cholesky(d["T_AA"][a])) < 1e-13
+    assert list(np.nonzero(fail_flags(d["T_AA"]))[0]) == list(w.indefinite)
+
+
+def test_cholesky_reads_lower_triangle_only_and_nan_fails():
+    T = synth.t_matrices(1, 8, ())[0][0]
+    Tl = np.tril(T) + np.triu(np.full_like(T, 1e300), 1)
+    L, ok = cholesky_lower(Tl)
+    assert ok and rel_frobenius(L @ L.conj().T, T) < 1e-14
+    Tn = T.copy()
+    Tn[3, 3] = np.nan
+    assert not cholesky_lower(Tn)[1]
+    Tz = np.zeros((4, 4), dtype=np.complex128)
+    assert not cholesky_lower(Tz)[1]
+
+
+def test_indefinite_recipe_spreads_atoms():
+    assert synth.indefinite_atoms(100, 0.05) == (3, 23, 43, 63, 83)
+    assert synth.indefinite_atoms(256, 0.02) == (3, 54, 105, 156, 207)
+    assert synth.WORKLOADS["tiny"].indefinite == (3,)
