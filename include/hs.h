@@ -1,0 +1,151 @@
+/*
+ * libhs -- GB300 (sm_103a) assembly of the FLAPW Hamiltonian H and overlap S
+ * for one k-point.
+ *
+ *   H = sum_a A_a^H T^AA_a A_a + A_a^H T^AB_a B_a + B_a^H T^BA_a A_a + B_a^H T^BB_a B_a   (Eq. (h))
+ *   S = sum_a A_a^H A_a + B_a^H U_a^H U_a B_a                                              (Eq. (s))
+ *
+ * Shapes (Sec. 2, after Eq. (s)): A_a, B_a in C^{N_L x N_G}; T_a in C^{N_L x N_L};
+ * H, S in C^{N_G x N_G}; U_a diagonal.  K = N_A * N_L.
+ *
+ * Method (Algorithm 1, restated for the GPU):
+ *   Z_a = T^BA_a A_a + 1/2 T^BB_a B_a,   H  = Z^H B + B^H Z          (first part of H)
+ *   S   = A^H A + (U B)^H (U B)                                        (S)
+ *   T^AA_a = C_a C_a^H (Cholesky): Y_a = C_a^H A_a,  H += Y^H Y         (second part of H)
+ *   Cholesky fails:                X_a = T^AA_a A_a, H += A_a^H X_a
+ * T^BA is not an input: Sec. 2 states T^BA = (T^AB)^H and that T^BB is Hermitian.
+ *
+ * ---------------------------------------------------------------------------
+ * Memory layout (all matrices column-major, BLAS order; complex = interleaved
+ * re, im doubles, layout-compatible with cuDoubleComplex / std::complex<double>):
+ *   A, B    : K x N_G, leading dimension K.  Atom a owns rows [a*N_L, (a+1)*N_L).
+ *   T_AA, T_AB, T_BB : N_A consecutive N_L x N_L column-major blocks (stride N_L^2).
+ *             Only the LOWER triangle of T_AA and T_BB is read (zpotrf / zhemm
+ *             semantics); T_AB is read in full.
+ *   U       : N_A x N_L reals, U[a*N_L + L] is the diagonal entry of U_a.
+ *   H, S    : N_G x N_G, leading dimension N_G.  Both triangles are written;
+ *             the result is exactly Hermitian with exactly real diagonal.
+ *
+ * Ownership: the caller owns every input and output buffer.  Buffers must stay
+ * valid and unmodified until the call that uses them completes (hs_assemble
+ * returns, or hs_poll returns HS_OK for the ticket).  The plan owns its device
+ * workspace and a cache of the factorised T^AA blocks, keyed by the T pointers:
+ * after changing T contents in place, call hs_set_t() (or pass new pointers).
+ *
+ * Errors: functions return HS_OK (0) or a negative code; no partial output is
+ * guaranteed after an error.  An atom whose Cholesky factorisation fails is NOT
+ * an error: it takes the fallback product and is counted in hs_info.n_fallback.
+ * Non-finite inputs are not checked and propagate as NaN.  Device-side waits
+ * are bounded; an expired wait returns HS_EDEVICE instead of hanging.
+ * Every entry point is thread-safe per plan (calls on one plan serialise).
+ */
+#ifndef HS_H_
+#define HS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hs_plan_s* hs_plan_t;
+
+/* One complex double, interleaved. */
+typedef struct { double re, im; } hs_z;
+
+enum {
+  HS_OK = 0,
+  HS_PENDING = 1,      /* hs_poll: ticket not finished yet */
+  HS_EINVAL = -1,      /* bad argument (sizes, null pointers, unknown precision) */
+  HS_ENOMEM = -2,      /* device allocation failed, or request above the HBM budget */
+  HS_ECUDA = -3,       /* a CUDA runtime call failed */
+  HS_EBUSY = -4,       /* serving queue full */
+  HS_ETIMEDOUT = -5,   /* hs_poll: timeout expired before completion */
+  HS_EDEVICE = -6,     /* a kernel set the device error word (bounded wait expired) */
+  HS_ENOTSUP = -7      /* feature not available for this plan */
+};
+
+/* Arithmetic of the big stacked contractions (the per-atom Cholesky and
+ * the final H/S values are FP64 in every mode). */
+enum {
+  HS_FP64 = 0,        /* plain FP64 everywhere */
+  HS_SPLIT_BF16 = 1   /* Ozaki-style slices on BF16 tensor cores (tcgen05), FP32
+                         exact windows, recombined in extended precision to FP64 */
+};
+
+typedef struct {
+  int n_fallback;      /* atoms whose Cholesky failed (Algorithm 1 failure branch) */
+  int slices;          /* slice count used (0 for HS_FP64) */
+  double ms_total;     /* device time of the whole call (CUDA events) */
+  double ms_factor;    /* Cholesky + T preparation (0 when served from the cache) */
+  double ms_atoms;     /* per-atom products Z, Y, X */
+  double ms_slice;     /* slicing of the contraction operands (split mode) */
+  double ms_S;         /* S contraction */
+  double ms_H;         /* H contraction */
+  double ms_finalize;  /* mirror to the upper triangle, real diagonal */
+} hs_info;
+
+/* Create a plan for problems with N_A atoms, N_L = (l_max+1)^2 and N_G <= N_G_max.
+ * precision: HS_FP64 or HS_SPLIT_BF16.  slices: 2..8 for split mode (0 = default 5),
+ * ignored for FP64.  hbm_budget_bytes: cap on the plan's device workspace plus the
+ * H/S outputs of requests in flight (serving admission); 0 = no cap.
+ * stream: cudaStream_t to run on (NULL = the legacy default stream).
+ * Allocates the device workspace for N_G_max up front; returns HS_ENOMEM if it
+ * does not fit.  Sizes: N_A >= 1, 1 <= N_L <= 256, N_G_max >= 1. */
+int hs_plan(hs_plan_t* out, int N_A, int N_L, int N_G_max, int precision, int slices,
+            size_t hbm_budget_bytes, void* stream);
+
+/* Exact device bytes one assembly of width N_G needs: the plan's workspace share
+ * plus the caller's H and S (2 * 16 * N_G^2).  0 for a bad plan or N_G. */
+size_t hs_footprint(hs_plan_t plan, int N_G);
+
+/* Factorise T^AA (batched FP64 Cholesky, Algorithm 1 "try Cholesky") and prepare
+ * the per-atom operators from device pointers T_AA, T_AB, T_BB (layout above).
+ * Called implicitly by hs_assemble when the T pointers differ from the cached
+ * ones; call it explicitly after changing T contents in place. */
+int hs_set_t(hs_plan_t plan, const hs_z* T_AA, const hs_z* T_AB, const hs_z* T_BB);
+
+/* Assemble H and S for one k-point (Eqs. (h), (s)).  All pointers are DEVICE
+ * pointers (layout above).  Blocks until H and S are complete.  N_A and N_L
+ * must equal the plan's; 1 <= N_G <= N_G_max.  info may be NULL. */
+int hs_assemble(hs_plan_t plan, const hs_z* A, const hs_z* B,
+                const hs_z* T_AA, const hs_z* T_AB, const hs_z* T_BB, const double* U,
+                int N_A, int N_L, int N_G, hs_z* H, hs_z* S, hs_info* info);
+
+/* Same as hs_assemble with HOST buffers: the call copies A, B, T, U to the device
+ * (staging buffers owned by the plan, allocated on first use), assembles, and
+ * copies H and S back.  Pinned host memory gives the fastest copies. */
+int hs_assemble_host(hs_plan_t plan, const hs_z* A, const hs_z* B,
+                     const hs_z* T_AA, const hs_z* T_AB, const hs_z* T_BB, const double* U,
+                     int N_A, int N_L, int N_G, hs_z* H, hs_z* S, hs_info* info);
+
+/* Serving: enqueue one k-point request (device pointers, layout above; A and B
+ * may be column-truncated views of wider arrays: ld_AB >= K is their leading
+ * dimension).  T and U must be the plan's current T (hs_set_t) and a U of the
+ * plan's shape.  Returns at once with a ticket.  The request is admitted to the
+ * device when its footprint fits the HBM budget and a slot is free; admitted
+ * requests run concurrently.  HS_ENOMEM: footprint above the whole budget (can
+ * never be admitted).  HS_EBUSY: queue full. */
+int hs_submit(hs_plan_t plan, const hs_z* A, const hs_z* B, int ld_AB, const double* U,
+              int N_G, hs_z* H, hs_z* S, int64_t* ticket);
+
+/* Wait up to timeout_us microseconds (0 = just test, <0 = no limit) for a ticket.
+ * HS_OK: done (info filled if non-NULL; the ticket is retired).  HS_PENDING /
+ * HS_ETIMEDOUT: not yet.  Negative: the request failed. */
+int hs_poll(hs_plan_t plan, int64_t ticket, int64_t timeout_us, hs_info* info);
+
+/* Copy the per-atom Cholesky failure flags of the cached factorisation to
+ * flags_host[N_A] (1 = fallback product used). */
+int hs_fallback_flags(hs_plan_t plan, int* flags_host);
+
+/* Free the plan and its workspace (waits for requests in flight). */
+int hs_destroy(hs_plan_t plan);
+
+/* Static description of an error code. */
+const char* hs_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HS_H_ */
