@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark: H+S assembly for one k-point per step on GB300.
+
+A step is one full pass of the hot path on one k-point: factorise T^AA
+(batched Cholesky + failure test; redone every step, nothing cached across
+steps), the per-atom products, the slicing of the stacked operands (split
+form), the S and H contractions and the final mirror -- through the C-ABI
+call ``hs_assemble`` on inputs already resident in HBM.
+
+Workload: ``auag_like_4000`` (N_A=100, N_L=121 = (10+1)^2, N_G=4000, 5 of
+100 atoms with indefinite T^AA), synthetic inputs shaped like the paper's
+AuAg case (Tab. 1).  Every input is larger than L2 (A, B: 0.77 GB each), so
+no L2 flush is needed between steps.
+
+Value: algorithmic TFLOP/s (Algorithm 1 flop count, ``flops.assembly_flops``)
+of the split-precision form; the plain FP64 GPU form is timed in the same
+run and reported beside it.  ``e2e`` repeats the measurement through
+``hs_assemble_host`` with pinned host buffers (copies inside the timed
+region).  Under torchrun every rank assembles its own k-points (k-points are
+independent: weak scaling, no collective on the data path).
+
+``--impl reference`` times the CPU FP64 oracle on the host cores on a
+bounded column panel of the same workload (the only other use of oracle/).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1611_00606_gb300 import flops as _flops  # noqa: E402
+from paper_1611_00606_gb300 import synth  # noqa: E402
+
+METRIC = "H+S assembly TFLOP/s (Algorithm 1 flop count) per k-point, split-precision form"
+UNIT = "TFLOP/s"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+
+
+def _peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, w):
+    """CPU FP64 oracle on a bounded column panel per step (rank 0 only)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import assemble
+    d = synth.make_inputs(w)
+    N_f = len(w.indefinite)
+    F = _flops.assembly_flops(w.N_A, w.N_L, w.N_G, N_f)
+    ncols = args.ref_cols
+    cols = np.arange(ncols)
+
+    def step():
+        t0 = time.perf_counter()
+        assemble(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], w.N_A, w.N_L,
+                 cols=cols)
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        step()
+    ts = [step() for _ in range(args.steps)]
+    t = sum(ts)
+    value = F * (ncols / w.N_G) * args.steps / t / 1e12
+    sample = f"oracle column panel H[:, :{ncols}], S[:, :{ncols}] of {w.name} per step"
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": _wl_desc(w), "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def _wl_desc(w):
+    return (f"{w.name} (N_A={w.N_A}, N_L={w.N_L}, N_G={w.N_G}, "
+            f"{len(w.indefinite)} indefinite T_AA)")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="auag_like_4000", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp64"])
+    ap.add_argument("--slices", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the FP64 form (0: skip)")
+    ap.add_argument("--ref-cols", type=int, default=48, help="oracle panel width per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1611_00606_gb300 import hs
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    N_f = len(w.indefinite)
+    F = _flops.assembly_flops(w.N_A, w.N_L, w.N_G, N_f)
+    K = w.K
+    # each rank draws its own k-point (seed offset by rank): independent problems
+    wr = synth.Workload(w.name, w.N_A, w.N_L, w.N_G, w.indefinite, w.seed + rank)
+    d = synth.make_inputs(wr)
+    A, B = hs.to_device_coef(d["A"], dev), hs.to_device_coef(d["B"], dev)
+    T = [hs.to_device_T(d[k], dev) for k in ("T_AA", "T_AB", "T_BB")]
+    U = hs.to_device_U(d["U"], dev)
+    H, S = hs.empty_hs(w.N_G, dev), hs.empty_hs(w.N_G, dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed_loop(plan, steps, warmup, infos):
+        def one():
+            hs.hs_set_t(plan, *T)  # factor every step: no cache across k-points
+            _, _, info = hs.hs_assemble(plan, A, B, *T, U, w.N_A, w.N_L, w.N_G, H, S)
+            return info
+        for _ in range(warmup):
+            one()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            infos.append(one())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # ---------------- main form (device-resident inputs)
+    plan = hs.hs_plan(w.N_A, w.N_L, w.N_G, args.precision, args.slices if
+                      args.precision == "split_bf16" else 0, 0, stream)
+    clk = ClockSampler(torch.cuda.current_device())
+    infos = []
+    clk.start()
+    ms = timed_loop(plan, args.steps, args.warmup, infos)
+    clocks = clk.stop()
+    kpts = ws * args.steps / (ms / 1e3)
+    value = F * ws * args.steps / (ms / 1e3) / 1e12
+    ms_step = ms / args.steps
+
+    # roofline of the dominant kernel (H contraction), per-launch CUDA-event time
+    peaks, peak_src = _peaks()
+    ms_H = statistics.mean(i["ms_H"] for i in infos)
+    ms_S = statistics.mean(i["ms_S"] for i in infos)
+    st = _flops.step_flops(w.N_A, w.N_L, w.N_G, N_f)
+    F_H = st["H1_zher2k"] + st["H2_zgemm"] + st["H3_zherk"]
+    if args.precision == "split_bf16":
+        s = args.slices
+        pairs = s * (s + 1) // 2
+        achieved = pairs * F_H / (ms_H / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        roof = {"bound": "tensor", "kernel": "k_contract_split (H)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "work": f"{pairs} slice pairs x Algorithm 1 flops of H1+H2+H3 (BF16 tensor)",
+                "peak_source": f"bf16_tflops_sustained ({peak_src})"}
+    else:
+        achieved = F_H / (ms_H / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_contract_fp64 (H)", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "work": "Algorithm 1 flops of H1+H2+H3 (FP64 DFMA)",
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
+    launches_per_step = 2 + 1 + (1 if N_f else 0) + 2 + 2 + (1 if args.precision ==
+                                                                 "split_bf16" else 0)
+
+    # ---------------- plain FP64 GPU form, same run
+    fp64 = None
+    if args.precision == "split_bf16" and args.fp64_steps > 0:
+        p64 = hs.hs_plan(w.N_A, w.N_L, w.N_G, "fp64", 0, 0, stream)
+        inf64 = []
+        ms64 = timed_loop(p64, args.fp64_steps, 1, inf64)
+        hs.hs_destroy(p64)
+        fp64 = {"tflops": F * ws * args.fp64_steps / (ms64 / 1e3) / 1e12,
+                "kpts_per_s": ws * args.fp64_steps / (ms64 / 1e3),
+                "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
+
+    # ---------------- end to end through hs_assemble_host (pinned host buffers)
+    e2e = None
+    if not args.no_e2e:
+        def pin(t):  # pinned host copy with the same (column-major) strides
+            h = torch.empty_strided(t.shape, t.stride(), dtype=t.dtype, pin_memory=True)
+            h.copy_(t)
+            return h
+        hA, hB, hU = pin(A), pin(B), pin(U)
+        hT = [[pin(t) for t in T], [pin(t) for t in T]]  # two copies: re-factor each step
+        hH = torch.empty((w.N_G, w.N_G), dtype=torch.complex128, pin_memory=True).T
+        hS = torch.empty((w.N_G, w.N_G), dtype=torch.complex128, pin_memory=True).T
+        ph = hs.hs_plan(w.N_A, w.N_L, w.N_G, args.precision,
+                        args.slices if args.precision == "split_bf16" else 0, 0, stream)
+        e_steps = max(2, args.steps // 2)
+        for i in range(2):
+            hs.hs_assemble_host(ph, hA, hB, *hT[i % 2], hU, w.N_A, w.N_L, w.N_G, hH, hS)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(e_steps):
+            hs.hs_assemble_host(ph, hA, hB, *hT[i % 2], hU, w.N_A, w.N_L, w.N_G, hH, hS)
+        torch.cuda.synchronize()
+        t_e = time.perf_counter() - t0
+        hs.hs_destroy(ph)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([t_e], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e = float(t.item())
+        h2d = 16 * K * w.N_G * 2 + 8 * K + 3 * 16 * w.N_A * w.N_L * w.N_L
+        e2e = {"value": F * ws * e_steps / t_e / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 2 * 16 * w.N_G * w.N_G, "steps": e_steps,
+               "kpts_per_s": ws * e_steps / t_e}
+
+    # ---------------- CPU oracle baseline (rank 0, N=1 only) + sampled error
+    cpu = None
+    err = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import assemble, rel_frobenius
+        Hn = H.cpu().numpy()
+        Sn = S.cpu().numpy()
+        ncols = args.ref_cols
+        cols = np.arange(ncols)
+        t0 = time.perf_counter()
+        Hr, Sr = assemble(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], w.N_A,
+                          w.N_L, cols=cols)
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": F * (ncols / w.N_G) / t_cpu / 1e12, "unit": UNIT,
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"oracle column panel H[:, :{ncols}], S[:, :{ncols}] of {w.name} "
+                         f"({t_cpu:.1f} s), scaled by N_G/{ncols}"}
+        err = {"H": rel_frobenius(Hn[:, cols], Hr), "S": rel_frobenius(Sn[:, cols], Sr),
+               "columns": f"0..{ncols - 1}"}
+
+    hs.hs_destroy(plan)
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": (f"bf16 slices x{args.slices}, fp32 windows, fp64 result"
+                      if args.precision == "split_bf16" else "f64"),
+            "data": "synthetic",
+            "config": {"workload": _wl_desc(w), "precision": args.precision,
+                       "slices": args.slices if args.precision == "split_bf16" else 0,
+                       "step": "factor T_AA + per-atom products + slicing + S, H contractions"
+                               " + mirror, one k-point",
+                       "l2": "inputs larger than L2 (A, B 0.77 GB each), no flush needed",
+                       "parallelism": f"replicas x{ws} (independent k-points)"},
+            "kpts_per_s": kpts,
+            "phase_ms": {k: statistics.mean(i[k] for i in infos) for k in
+                         ("ms_factor", "ms_atoms", "ms_slice", "ms_S", "ms_H", "ms_finalize")},
+            "fp64_form": fp64,
+            "speedup_vs_fp64_form": (value / fp64["tflops"]) if fp64 else None,
+            "max_rel_frobenius_sampled": err,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -87,12 +87,12 @@ typedef struct {
 } hs_info;
 
 /* Create a plan for problems with N_A atoms, N_L = (l_max+1)^2 and N_G <= N_G_max.
- * precision: HS_FP64 or HS_SPLIT_BF16.  slices: 2..8 for split mode (0 = default 5),
+ * precision: HS_FP64 or HS_SPLIT_BF16.  slices: 2..7 for split mode (0 = default 5),
  * ignored for FP64.  hbm_budget_bytes: cap on the plan's device workspace plus the
  * H/S outputs of requests in flight (serving admission); 0 = no cap.
  * stream: cudaStream_t to run on (NULL = the legacy default stream).
  * Allocates the device workspace for N_G_max up front; returns HS_ENOMEM if it
- * does not fit.  Sizes: N_A >= 1, 1 <= N_L <= 256, N_G_max >= 1. */
+ * does not fit.  Sizes: N_A >= 1, 1 <= N_L <= 168, N_G_max >= 1. */
 int hs_plan(hs_plan_t* out, int N_A, int N_L, int N_G_max, int precision, int slices,
             size_t hbm_budget_bytes, void* stream);
 

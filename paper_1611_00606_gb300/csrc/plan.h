@@ -15,7 +15,7 @@
 
 constexpr int kMaxNL = 168;       // packed lower triangle of T^AA fits in 227 KB smem
 constexpr int kDefaultSlices = 5;
-constexpr int kMaxSlices = 8;
+constexpr int kMaxSlices = 7;  // 7 + 9*(s-1) bits must fit an int64 digit word
 
 struct SplitWork;   // k_split.cu
 struct ServeState;  // serve.cu

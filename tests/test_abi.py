@@ -57,7 +57,7 @@ def test_strerror_and_argument_validation(lib):
     assert lib.hs_plan(C.byref(h), 4, 16, 0, 0, 0, C.c_size_t(0), None) == -1
     assert lib.hs_plan(C.byref(h), 4, 16, 100, 9, 0, C.c_size_t(0), None) == -1
     assert lib.hs_plan(C.byref(h), 4, 16, 100, 1, 1, C.c_size_t(0), None) == -1
-    assert lib.hs_plan(C.byref(h), 4, 16, 100, 1, 9, C.c_size_t(0), None) == -1
+    assert lib.hs_plan(C.byref(h), 4, 16, 100, 1, 8, C.c_size_t(0), None) == -1
     assert lib.hs_plan(None, 4, 16, 100, 0, 0, C.c_size_t(0), None) == -1
     lib.hs_footprint.restype = C.c_size_t
     assert lib.hs_footprint(None, 10) == 0

@@ -1,0 +1,115 @@
+"""Parity of the split-precision form (BF16 tcgen05 slices, FP64 recombination)
+with the CPU FP64 oracle.
+
+The stated bound for the split form is a relative Frobenius error <= 1e-10
+against the oracle at the default slice count (5).  Fewer slices must give
+a monotonically larger error (each slice carries 9 more bits), which pins
+that every slice-pair level reaches the accumulators.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import assemble, fail_flags, rel_frobenius  # noqa: E402
+from paper_1611_00606_gb300 import synth  # noqa: E402
+
+TOL_SPLIT = 1e-10
+
+
+@pytest.fixture(scope="module")
+def hs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_00606_gb300 import hs as _hs
+    return _hs
+
+
+def _run(hs, d, N_A, N_L, slices=0, precision="split_bf16"):
+    N_G = d["A"].shape[1]
+    A, B = hs.to_device_coef(d["A"]), hs.to_device_coef(d["B"])
+    T = [hs.to_device_T(d[k]) for k in ("T_AA", "T_AB", "T_BB")]
+    U = hs.to_device_U(d["U"])
+    with hs.Plan(N_A, N_L, N_G, precision, slices) as p:
+        H, S, info = p.assemble(A, B, *T, U)
+        flags = hs.hs_fallback_flags(p.h, N_A)
+    torch.cuda.synchronize()
+    return H.cpu().numpy(), S.cpu().numpy(), info, flags
+
+
+@pytest.mark.parametrize("N_A,N_L,N_G,indef", [
+    (4, 16, 256, (3,)),        # tiny workload
+    (1, 1, 1, ()),             # one atom, one L, one G
+    (3, 9, 7, (1,)),
+    (2, 5, 65, ()),            # one 64-column tile plus a 1-wide tail
+    (5, 16, 257, (0, 4)),      # several 128-row tiles, ragged tail
+    (3, 33, 130, (0, 1, 2)),   # every atom fails: no Y segment
+    (2, 121, 300, (1,)),       # K per segment = 242 complex: windows straddle atoms
+])
+def test_split_full_parity(hs, N_A, N_L, N_G, indef):
+    d = synth.make_inputs(synth.Workload("s", N_A, N_L, N_G, indef, seed=N_G + 1))
+    H, S, info, flags = _run(hs, d, N_A, N_L)
+    Hr, Sr = assemble(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], N_A, N_L)
+    assert rel_frobenius(H, Hr) <= TOL_SPLIT
+    assert rel_frobenius(S, Sr) <= TOL_SPLIT
+    assert np.array_equal(flags, fail_flags(d["T_AA"]))
+    assert info["slices"] == 5 and info["n_fallback"] == len(indef)
+    assert np.array_equal(H, H.conj().T) and np.array_equal(S, S.conj().T)
+
+
+def test_error_decreases_with_slices(hs):
+    N_A, N_L, N_G = 4, 16, 256
+    d = synth.make_inputs(synth.Workload("e", N_A, N_L, N_G, (3,), seed=11))
+    Hr, Sr = assemble(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], N_A, N_L)
+    errs = []
+    for s in range(2, 8):
+        H, S, info, _ = _run(hs, d, N_A, N_L, slices=s)
+        assert info["slices"] == s
+        errs.append(max(rel_frobenius(H, Hr), rel_frobenius(S, Sr)))
+    # each extra slice adds ~9 bits until FP64 rounding of the oracle dominates
+    for a, b in zip(errs[:3], errs[1:4]):
+        assert b < a / 16
+    assert errs[3] <= TOL_SPLIT  # s = 5
+    assert max(errs[4:]) <= 1e-12
+
+
+def test_split_matches_fp64_form_and_is_deterministic(hs):
+    N_A, N_L, N_G = 6, 25, 400
+    d = synth.make_inputs(synth.Workload("d", N_A, N_L, N_G, (2,), seed=12))
+    H1, S1, _, _ = _run(hs, d, N_A, N_L)
+    H2, S2, _, _ = _run(hs, d, N_A, N_L)
+    assert np.array_equal(H1, H2) and np.array_equal(S1, S2)
+    Hf, Sf, _, _ = _run(hs, d, N_A, N_L, precision="fp64")
+    assert rel_frobenius(H1, Hf) <= TOL_SPLIT and rel_frobenius(S1, Sf) <= TOL_SPLIT
+
+
+def test_split_nan_propagates(hs):
+    N_A, N_L, N_G = 2, 4, 10
+    d = synth.make_inputs(synth.Workload("n", N_A, N_L, N_G, (), seed=6))
+    d["A"] = d["A"].copy(order="F")
+    d["A"][2, 3] = np.nan
+    H, S, _, _ = _run(hs, d, N_A, N_L)
+    assert np.isnan(H[:, 3]).any() and np.isnan(S[:, 3]).any()
+    assert np.isfinite(S[np.ix_([0, 1, 2, 4], [0, 1, 2, 4])]).all()
+
+
+def _panel_cols(N_G, width=16):
+    mid = N_G // 2
+    return np.concatenate([np.arange(0, width), np.arange(mid - width // 2, mid + width // 2),
+                           np.arange(N_G - width, N_G)])
+
+
+def test_split_paper_scale_panels(hs):
+    """auag_like_4000 in the benchmark's launch configuration; oracle panels."""
+    w = synth.WORKLOADS["auag_like_4000"]
+    d = synth.make_inputs(w)
+    H, S, info, flags = _run(hs, d, w.N_A, w.N_L)
+    cols = _panel_cols(w.N_G)
+    Hr, Sr = assemble(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], w.N_A, w.N_L,
+                      cols=cols)
+    eh, es = rel_frobenius(H[:, cols], Hr), rel_frobenius(S[:, cols], Sr)
+    print(f"auag_like_4000 split s=5: H {eh:.3e} S {es:.3e}")
+    assert eh <= TOL_SPLIT and es <= TOL_SPLIT
+    assert list(np.nonzero(flags)[0]) == list(w.indefinite)
