@@ -236,6 +236,7 @@ def main():
     clk.start()
     ms = timed_loop(plan, args.steps, args.warmup, infos)
     clocks = clk.stop()
+    snap = {args.precision: (H.cpu().numpy(), S.cpu().numpy())}
     kpts = ws * args.steps / (ms / 1e3)
     value = F * ws * args.steps / (ms / 1e3) / 1e12
     ms_step = ms / args.steps
@@ -272,6 +273,7 @@ def main():
         inf64 = []
         ms64 = timed_loop(p64, args.fp64_steps, 1, inf64)
         hs.hs_destroy(p64)
+        snap["fp64"] = (H.cpu().numpy(), S.cpu().numpy())
         fp64 = {"tflops": F * ws * args.fp64_steps / (ms64 / 1e3) / 1e12,
                 "kpts_per_s": ws * args.fp64_steps / (ms64 / 1e3),
                 "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
@@ -315,8 +317,6 @@ def main():
     err = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import assemble, rel_frobenius
-        Hn = H.cpu().numpy()
-        Sn = S.cpu().numpy()
         ncols = args.ref_cols
         cols = np.arange(ncols)
         t0 = time.perf_counter()
@@ -327,8 +327,9 @@ def main():
                "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"oracle column panel H[:, :{ncols}], S[:, :{ncols}] of {w.name} "
                          f"({t_cpu:.1f} s), scaled by N_G/{ncols}"}
-        err = {"H": rel_frobenius(Hn[:, cols], Hr), "S": rel_frobenius(Sn[:, cols], Sr),
-               "columns": f"0..{ncols - 1}"}
+        err = {form: {"H": rel_frobenius(Hn[:, cols], Hr), "S": rel_frobenius(Sn[:, cols], Sr)}
+               for form, (Hn, Sn) in snap.items()}
+        err["columns"] = f"0..{ncols - 1}"
 
     hs.hs_destroy(plan)
     if rank == 0:

@@ -11,12 +11,16 @@
 // with E_g chosen per column from the column's largest component (so that
 // max|x|/2^E_g lies in [64, 128)).  Every d_p * 2^{-9(p-1)} is exact in
 // BF16.  Products of two slices are exact; summed over a window of 256 real K
-// the slice-pair levels 0 (d_1 e_1) and 1 (d_1 e_2 + d_2 e_1) stay below 2^24
-// units and are therefore exact in the FP32 tensor-core accumulators.
-// Levels >= 2 (2^-18 and below) are accumulated together, inexactly.  After
-// every window the three accumulators are drained from TMEM into a
-// double-float (hi, lo FP32 pair) accumulator per output element, scaled by
-// 2^{E_i + E_j}; the pair is summed to FP64 once per tile at the end.
+// of 128 real K the slice-pair levels 0 (d_1 e_1), 1 (d_1 e_2 + d_2 e_1) and
+// 2 (d_1 e_3 + d_2 e_2 + d_3 e_1) stay within 2^24 units and are therefore
+// exact in FP32 tensor-core accumulators, whatever the accumulator's rounding.
+// Levels >= 3 (2^-27 and below) share a fourth, inexact accumulator.  After
+// every window the four TMEM accumulators are drained into a double-float
+// (hi, lo FP32 pair) accumulator per output element, scaled by 2^{E_i + E_j}:
+// levels 0, 1 and 2 through an error-free TwoSum into hi, levels >= 3 into lo
+// (the leading digit is typically small, so level 2 is only ~2^-14 below
+// level 0 and would cap the pair's precision if it went to lo directly).
+// The pair is summed to FP64 once per tile at the end.
 //
 // Complex arithmetic on real tensor cores: with the K-major interleaved
 // (re, im) storage, Re(L^H R) = L'^T R' and Im(L^H R) = L'^T R'' where R''
@@ -37,7 +41,7 @@ constexpr int BM = 128;        // complex rows per tile (MMA M)
 constexpr int BNC = 64;        // complex columns per tile
 constexpr int BN = 2 * BNC;    // MMA N (Re | Im)
 constexpr int KB = 16;         // real K per pipeline stage (= one MMA K step)
-constexpr int WIN = 16;        // stages per exact window (256 real K)
+constexpr int WIN = 8;         // stages per exact window (128 real K)
 constexpr int ROWS_ALIGN = 128;
 constexpr int kMaxMaps = 13;
 constexpr int kMaxJobs = 7;
@@ -124,14 +128,13 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uin
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                 "=r"(r[6]), "=r"(r[7])
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr));
 #pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -165,24 +168,26 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 }
 
 
-// Drain one 32-column strip of the three window accumulators (level 0 at
-// column offset 0, level 1 at BN, levels >= 2 at 2*BN) into (hi, lo) pairs,
-// scaled by 2^(eL + eR[c]); lane c of eRl holds column c's exponent.
-__device__ __forceinline__ void drain_cols(uint32_t taddr, int s, int eL, int eRl,
+// Drain one 32-column strip of the four window accumulators (level k at
+// column offset k*BN) into (hi, lo) pairs.  rsc = 2^eL (this thread's row);
+// lane c of csc holds 2^eR of column c.
+__device__ __forceinline__ void drain_cols(uint32_t taddr, int s, float rsc, float csc,
                                            float (&hi)[32], float (&lo)[32]) {
 #pragma unroll
-  for (int c0 = 0; c0 < 32; c0 += 8) {
-    float v0[8], v1[8], v2[8];
-    tmem_ld8(taddr + c0, v0);
-    tmem_ld8(taddr + BN + c0, v1);
-    if (s >= 3) tmem_ld8(taddr + 2 * BN + c0, v2);
+  for (int c0 = 0; c0 < 32; c0 += 4) {
+    float v0[4], v1[4], v2[4], v3[4];
+    tmem_ld4(taddr + c0, v0);
+    tmem_ld4(taddr + BN + c0, v1);
+    if (s >= 3) tmem_ld4(taddr + 2 * BN + c0, v2);
+    if (s >= 4) tmem_ld4(taddr + 3 * BN + c0, v3);
     tmem_wait_ld();
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const float sc = pow2f(eL + __shfl_sync(0xffffffffu, eRl, c0 + c));
+    for (int c = 0; c < 4; ++c) {
+      const float sc = rsc * __shfl_sync(0xffffffffu, csc, c0 + c);
       two_sum_acc(hi[c0 + c], lo[c0 + c], v0[c] * sc);
       two_sum_acc(hi[c0 + c], lo[c0 + c], v1[c] * sc);
-      if (s >= 3) lo[c0 + c] += v2[c] * sc;
+      if (s >= 3) two_sum_acc(hi[c0 + c], lo[c0 + c], v2[c] * sc);
+      if (s >= 4) lo[c0 + c] = fmaf(v3[c], sc, lo[c0 + c]);
     }
   }
 }
@@ -343,7 +348,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
               const uint64_t ad = sdesc_sw32(sa + p * 2 * TILE_BYTES);
               for (int q = 0; p + q < s; ++q) {
                 const int lvl = p + q;
-                const int acc = lvl < 2 ? lvl : 2;
+                const int acc = lvl < 3 ? lvl : 3;
                 const bool init = first && p == 0 && q == acc;  // first pair of this level
                 tc_mma_bf16(tmem + acc * BN, ad, sdesc_sw32(sb + q * 2 * TILE_BYTES), kIdesc,
                             init ? 0u : 1u);
@@ -382,16 +387,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     bool ok = true;
     for (int sg = 0; sg < P.nseg && ok; ++sg) {
       const SplitSeg S = P.seg[sg];
-      const int eL = S.eL[row];
-      const int eRl = S.eR[j0 + 32 * h + lane];  // lane c holds column c's exponent
+      const float rsc = pow2f(S.eL[row]);
+      const float csc = pow2f(S.eR[j0 + 32 * h + lane]);  // lane c: column c's scale
       for (int w0 = 0; w0 < S.kblocks; w0 += WIN) {
         if (!mbar_wait(acc_full, (uint32_t)nwin & 1u, abort_flag)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        drain_cols(tl + (uint32_t)(32 * h), s, eL, eRl, hr, lr);            // Re
-        drain_cols(tl + (uint32_t)(BNC + 32 * h), s, eL, eRl, hi_, li);     // Im
+        drain_cols(tl + (uint32_t)(32 * h), s, rsc, csc, hr, lr);            // Re
+        drain_cols(tl + (uint32_t)(BNC + 32 * h), s, rsc, csc, hi_, li);     // Im
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acc_empty);
