@@ -74,6 +74,9 @@ WORKLOADS = {
     "auag_like_4000": Workload("auag_like_4000", 100, 121, 4000, indefinite_atoms(100, 0.05)),
     "large_12000": Workload("large_12000", 256, 144, 12000, indefinite_atoms(256, 0.02)),
     "split_8000": Workload("split_8000", 100, 121, 8000, indefinite_atoms(100, 0.05)),
+    # half the atoms of auag_like at N_G = 2048: every input still larger than
+    # L2, a few GB on the device in split mode (kernel profiling case)
+    "profile_2048": Workload("profile_2048", 50, 121, 2048, indefinite_atoms(50, 0.05)),
 }
 
 
