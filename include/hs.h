@@ -63,7 +63,8 @@ enum {
   HS_EBUSY = -4,       /* serving queue full */
   HS_ETIMEDOUT = -5,   /* hs_poll: timeout expired before completion */
   HS_EDEVICE = -6,     /* a kernel set the device error word (bounded wait expired) */
-  HS_ENOTSUP = -7      /* feature not available for this plan */
+  HS_ENOTSUP = -7,     /* feature not available for this plan */
+  HS_ESCRATCH = -8     /* hs_assemble_static: problem larger than its static scratch */
 };
 
 /* Arithmetic of the big stacked contractions (the per-atom Cholesky and
@@ -141,6 +142,34 @@ int hs_fallback_flags(hs_plan_t plan, int* flags_host);
 
 /* Free the plan and its workspace (waits for requests in flight). */
 int hs_destroy(hs_plan_t plan);
+
+/* ---------------------------------------------------------------------------
+ * Allocation-free FP64 assembly (a library addition; the paper has no
+ * counterpart).  For callers that may not allocate device memory -- code
+ * running under strict CUDA-graph capture, inside someone else's fixed memory
+ * arena, or in a host that locks its device footprint after start-up.  It runs
+ * the plain FP64 path of hs_assemble (same kernels, same results) without a
+ * plan: all intermediate buffers live in one file-scope device array of
+ * HS_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits.  Nothing is allocated and nothing is cached between calls.
+ *
+ * Pointers are DEVICE pointers with the layout above; stream is a cudaStream_t
+ * (NULL = legacy default stream).  Returns after H and S are complete.
+ * Size limit: the call needs
+ *   align256(16 N_A N_L^2) + align256(32 N_A N_L^2) + 3 align256(4 N_A) + 256
+ *   + 3 align256(16 N_A N_L N_G)
+ * bytes of scratch; above HS_STATIC_SCRATCH_BYTES it returns HS_ESCRATCH without
+ * touching the device.  1 <= N_L <= 168.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it: make that
+ * first call before any stream capture begins.  All calls on a device share
+ * the one array and each call overwrites it, so calls whose GPU work overlaps
+ * (other streams, other host threads) race and give wrong results: serialise
+ * them. */
+#define HS_STATIC_SCRATCH_BYTES (32u << 20)
+int hs_assemble_static(const hs_z* A, const hs_z* B, const hs_z* T_AA, const hs_z* T_AB,
+                       const hs_z* T_BB, const double* U, int N_A, int N_L, int N_G,
+                       hs_z* H, hs_z* S, void* stream);
 
 /* Static description of an error code. */
 const char* hs_strerror(int code);

@@ -26,6 +26,7 @@ extern "C" const char* hs_strerror(int code) {
     case HS_ETIMEDOUT: return "timed out";
     case HS_EDEVICE: return "device error word set (bounded wait expired)";
     case HS_ENOTSUP: return "not supported by this plan";
+    case HS_ESCRATCH: return "problem larger than the static scratch of hs_assemble_static";
     default: return "unknown error";
   }
 }

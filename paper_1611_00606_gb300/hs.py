@@ -26,6 +26,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhs.so")
 HS_OK, HS_PENDING = 0, 1
 HS_EINVAL, HS_ENOMEM, HS_ECUDA, HS_EBUSY, HS_ETIMEDOUT, HS_EDEVICE, HS_ENOTSUP = (
     -1, -2, -3, -4, -5, -6, -7)
+HS_ESCRATCH = -8
 HS_FP64, HS_SPLIT_BF16 = 0, 1
 PRECISIONS = {"fp64": HS_FP64, "split_bf16": HS_SPLIT_BF16}
 
@@ -54,6 +55,7 @@ SIGNATURES = {
     "hs_fallback_flags": (_I, [_VP, C.POINTER(_I)]),
     "hs_destroy": (_I, [_VP]),
     "hs_strerror": (C.c_char_p, [_I]),
+    "hs_assemble_static": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _VP, _VP, _VP]),
 }
 
 
@@ -226,6 +228,26 @@ def hs_fallback_flags(plan: int, N_A: int) -> np.ndarray:
 
 def hs_destroy(plan: int) -> None:
     _check(_lib.hs_destroy(plan), "hs_destroy")
+
+
+def hs_assemble_static(A, B, T_AA, T_AB, T_BB, U, N_A: int, N_L: int, N_G: int, H, S,
+                       stream=None) -> None:
+    """Allocation-free FP64 assembly (no plan): intermediates live in the library's
+    static device scratch.  For callers that must not allocate device memory; see
+    include/hs.h for the size limit and the rule that overlapping calls race."""
+    import torch
+    K = N_A * N_L
+    if _check_coef(A, K, N_G, "A") != K or _check_coef(B, K, N_G, "B") != K:
+        raise ValueError("hs_assemble_static: A and B must have leading dimension K")
+    for T, n in ((T_AA, "T_AA"), (T_AB, "T_AB"), (T_BB, "T_BB")):
+        _check_T(T, N_A, N_L, n)
+    _check_out(H, N_G, "H")
+    _check_out(S, N_G, "S")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(_lib.hs_assemble_static(_ptr(A), _ptr(B), _ptr(T_AA), _ptr(T_AB), _ptr(T_BB),
+                                   _ptr(U), N_A, N_L, N_G, _ptr(H), _ptr(S),
+                                   C.c_void_p(stream.cuda_stream)), "hs_assemble_static")
 
 
 def hs_strerror(code: int) -> str:

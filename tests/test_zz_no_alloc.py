@@ -1,0 +1,66 @@
+"""hs_assemble_static: the allocation-free FP64 assembly.
+
+Callers that may not allocate device memory (strict graph capture, fixed
+arenas, locked device footprints) use this entry point; its intermediates
+live in the library's static device scratch instead of a plan's workspace.
+Its H and S must match hs_assemble (FP64 plan) within the FP64 parity
+tolerance, on two calls in a row (the scratch keeps the previous call's
+contents, which must not leak into the next result).  This file is named to
+be collected last.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import rel_frobenius  # noqa: E402
+from paper_1611_00606_gb300 import synth  # noqa: E402
+
+TOL_FP64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def hs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_00606_gb300 import hs as _hs
+    return _hs
+
+
+def _device_inputs(hs, w):
+    d = synth.make_inputs(w)
+    return (hs.to_device_coef(d["A"]), hs.to_device_coef(d["B"]),
+            *[hs.to_device_T(d[k]) for k in ("T_AA", "T_AB", "T_BB")], hs.to_device_U(d["U"]))
+
+
+def test_static_entry_matches_plan_entry_on_consecutive_calls(hs):
+    cases = [synth.Workload("a", 4, 16, 256, (3,), seed=21),
+             synth.Workload("b", 3, 9, 100, (0, 2), seed=22),
+             synth.Workload("a", 4, 16, 256, (3,), seed=21)]  # repeat after a different call
+    for w in cases:
+        args = _device_inputs(hs, w)
+        with hs.Plan(w.N_A, w.N_L, w.N_G, "fp64") as p:
+            H_ref, S_ref, _ = p.assemble(*args)
+        for _ in range(2):  # two calls in a row on the same scratch
+            H = hs.empty_hs(w.N_G)
+            S = hs.empty_hs(w.N_G)
+            hs.hs_assemble_static(*args, w.N_A, w.N_L, w.N_G, H, S)
+            torch.cuda.synchronize()
+            Hn, Sn = H.cpu().numpy(), S.cpu().numpy()
+            assert rel_frobenius(Hn, H_ref.cpu().numpy()) <= TOL_FP64
+            assert rel_frobenius(Sn, S_ref.cpu().numpy()) <= TOL_FP64
+            assert np.array_equal(Hn, Hn.conj().T)
+
+
+def test_static_entry_rejects_problems_above_its_scratch(hs):
+    # K * N_G large enough that the three K x N_G buffers exceed the static array
+    N_A, N_L, N_G = 100, 121, 4000
+    K = N_A * N_L
+    A = torch.empty((N_G, 1), dtype=torch.complex128, device="cuda")  # never touched
+    rc = hs._lib.hs_assemble_static(A.data_ptr(), A.data_ptr(), A.data_ptr(), A.data_ptr(),
+                                    A.data_ptr(), A.data_ptr(), N_A, N_L, N_G,
+                                    A.data_ptr() + 16, A.data_ptr() + 32, None)
+    assert rc == hs.HS_ESCRATCH
+    assert 3 * 16 * K * N_G > 32 * 2 ** 20  # HS_STATIC_SCRATCH_BYTES in include/hs.h
