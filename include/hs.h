@@ -85,6 +85,10 @@ typedef struct {
   double ms_S;         /* S contraction */
   double ms_H;         /* H contraction */
   double ms_finalize;  /* mirror to the upper triangle, real diagonal */
+  double ms_queue;     /* hs_poll: submit -> admission (host clock) */
+  double ms_latency;   /* hs_poll: submit -> GPU completion (host clock) */
+  double inflight_bytes; /* hs_poll: footprint of all admitted requests right after
+                            this one was admitted (never above the budget) */
 } hs_info;
 
 /* Create a plan for problems with N_A atoms, N_L = (l_max+1)^2 and N_G <= N_G_max.

@@ -32,14 +32,15 @@ extern "C" const char* hs_strerror(int code) {
 }
 
 // ---------------------------------------------------------------------------
-// workspace sizing
+// workspace sizing and allocation
 
-size_t hs_plan_s::workspace_bytes(int N_G) const {
+size_t hs_plan_s::ws_bytes(int N_G, int n_fail) const {
   const size_t K = (size_t)N_A * N_L;
+  const size_t nf = (size_t)(n_fail > 0 ? n_fail : 1);
   size_t b = 0;
-  b += 2 * 16 * K * (size_t)N_G;                    // Z, W2 (= [Y; X])
-  b += 16 * (size_t)N_A * N_L * (size_t)N_G;          // AF (A rows of failing atoms), worst case
-  b += split_bytes(N_G);
+  b += 2 * 16 * K * (size_t)N_G;            // Z, W2 (= [Y; X])
+  b += 16 * nf * N_L * (size_t)N_G;         // AF (A rows of failing atoms)
+  b += split_ws_bytes(N_G, n_fail);
   return b;
 }
 
@@ -52,10 +53,52 @@ static void free_ptr(void*& p) {
   p = nullptr;
 }
 
+static void free_ws_ptr(void*& p, bool async, cudaStream_t st) {
+  if (p) {
+    if (async) cudaFreeAsync(p, st);
+    else cudaFree(p);
+  }
+  p = nullptr;
+}
+
+int hs_plan_s::ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st, bool async) {
+  const size_t K = (size_t)N_A * N_L;
+  const size_t nf = (size_t)(n_fail > 0 ? n_fail : 1);
+  w = Workspace{};
+  w.async = async;
+  w.N_G = N_G;
+  w.n_fail = (int)nf;
+  auto al = [&](void** ptr, size_t bytes) -> bool {
+    if (bytes == 0) bytes = 256;
+    return (async ? hs_malloc_async(ptr, bytes, st, hs_serve_pool(this)) : cudaMalloc(ptr, bytes)) ==
+           cudaSuccess;
+  };
+  bool ok = al((void**)&w.Z, 16 * K * N_G) && al((void**)&w.W2, 16 * K * N_G) &&
+            al((void**)&w.AF, 16 * nf * N_L * N_G);
+  if (ok) ok = split_ws_alloc(w, N_G, (int)nf, st, async) == HS_OK;
+  if (!ok) {
+    cudaGetLastError();
+    ws_free(w, st);
+    return HS_ENOMEM;
+  }
+  return HS_OK;
+}
+
+void hs_plan_s::ws_free(Workspace& w, cudaStream_t st) {
+  free_ws_ptr((void*&)w.Z, w.async, st);
+  free_ws_ptr((void*&)w.W2, w.async, st);
+  free_ws_ptr((void*&)w.AF, w.async, st);
+  for (auto& b : w.sb) {
+    free_ws_ptr((void*&)b.plain, w.async, st);
+    free_ws_ptr((void*&)b.rot, w.async, st);
+    free_ws_ptr((void*&)b.expo, w.async, st);
+  }
+  w.N_G = 0;
+  w.n_fail = 0;
+}
+
 void hs_plan_s::release() {
-  free_ptr((void*&)Z);
-  free_ptr((void*&)W2);
-  free_ptr((void*&)AF);
+  ws_free(ws, stream);
   free_ptr((void*&)M2);
   free_ptr((void*&)MZ);
   free_ptr((void*&)fail_d);
@@ -63,7 +106,6 @@ void hs_plan_s::release() {
   free_ptr((void*&)fail_list_d);
   free_ptr((void*&)err_d);
   for (auto& p : stage) free_ptr(p);
-  split_release();
   for (auto& e : ev)
     if (e) { cudaEventDestroy(e); e = nullptr; }
 }
@@ -93,9 +135,7 @@ extern "C" int hs_plan(hs_plan_t* out, int N_A, int N_L, int N_G_max, int precis
   p->budget = hbm_budget_bytes;
   p->stream = (cudaStream_t)stream;
   cudaGetDevice(&p->device);
-  const size_t K = (size_t)N_A * N_L;
-  const size_t need = p->workspace_bytes(N_G_max) + p->fixed_bytes();
-  if (hbm_budget_bytes && need > hbm_budget_bytes) {
+  if (hbm_budget_bytes && p->fixed_bytes() + p->ws_bytes(1, 1) > hbm_budget_bytes) {
     delete p;
     return HS_ENOMEM;
   }
@@ -104,15 +144,12 @@ extern "C" int hs_plan(hs_plan_t* out, int N_A, int N_L, int N_G_max, int precis
     return cudaMalloc(ptr, bytes) == cudaSuccess;
   };
   bool ok = true;
-  ok = ok && alloc((void**)&p->Z, 16 * K * N_G_max);
-  ok = ok && alloc((void**)&p->W2, 16 * K * N_G_max);
   ok = ok && alloc((void**)&p->M2, (size_t)16 * N_A * N_L * N_L);
   ok = ok && alloc((void**)&p->MZ, (size_t)32 * N_A * N_L * N_L);
   ok = ok && alloc((void**)&p->fail_d, sizeof(int) * N_A);
   ok = ok && alloc((void**)&p->slot_d, sizeof(int) * N_A);
   ok = ok && alloc((void**)&p->fail_list_d, sizeof(int) * N_A);
   ok = ok && alloc((void**)&p->err_d, sizeof(int) * 16);
-  ok = ok && (p->split_alloc() == HS_OK);
   for (auto& e : p->ev) ok = ok && (cudaEventCreate(&e) == cudaSuccess);
   if (!ok) {
     cudaGetLastError();
@@ -127,7 +164,8 @@ extern "C" int hs_plan(hs_plan_t* out, int N_A, int N_L, int N_G_max, int precis
 
 extern "C" size_t hs_footprint(hs_plan_t p, int N_G) {
   if (!p || N_G < 1 || N_G > p->N_G_max) return 0;
-  return p->workspace_bytes(N_G) + p->fixed_bytes() + (size_t)2 * 16 * N_G * (size_t)N_G;
+  const int nf = p->t_valid ? p->N_f : p->N_A;
+  return p->ws_bytes(N_G, nf) + (size_t)2 * 16 * N_G * (size_t)N_G;
 }
 
 int hs_plan_s::factor(const double2* T_AA, const double2* T_AB, const double2* T_BB) {
@@ -152,16 +190,6 @@ int hs_plan_s::factor(const double2* T_AA, const double2* T_AB, const double2* T
   HS_CUDA_TRY(cudaMemcpy(slot_d, slot.data(), sizeof(int) * N_A, cudaMemcpyHostToDevice));
   if (N_f)
     HS_CUDA_TRY(cudaMemcpy(fail_list_d, flist.data(), sizeof(int) * N_f, cudaMemcpyHostToDevice));
-  // AF holds the A rows of the failing atoms: (N_f*N_L) x N_G_max
-  if (N_f > af_atoms) {
-    free_ptr((void*&)AF);
-    if (cudaMalloc((void**)&AF, (size_t)16 * N_f * N_L * N_G_max) != cudaSuccess) {
-      cudaGetLastError();
-      af_atoms = 0;
-      return HS_ENOMEM;
-    }
-    af_atoms = N_f;
-  }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ev[1], ev[2]);
   last_factor_ms = ms;
@@ -175,30 +203,34 @@ int hs_plan_s::factor(const double2* T_AA, const double2* T_AB, const double2* T
 extern "C" int hs_set_t(hs_plan_t p, const hs_z* T_AA, const hs_z* T_AB, const hs_z* T_BB) {
   if (!p || !T_AA || !T_AB || !T_BB) return HS_EINVAL;
   std::lock_guard<std::mutex> lk(p->mu);
-  return p->factor((const double2*)T_AA, (const double2*)T_AB, (const double2*)T_BB);
+  if (p->serve_busy()) return HS_EBUSY;  // requests in flight use the cached factor
+  int rc = p->factor((const double2*)T_AA, (const double2*)T_AB, (const double2*)T_BB);
+  if (rc == HS_OK) p->factor_pending_info = true;
+  return rc;
 }
 
-// Enqueue the per-k-point path on p->stream (the T factor must be current).
-// ev[3..8] bracket the phases for hs_info.
+// Enqueue the per-k-point path on stream st using workspace w (the T factor
+// must be current).  ev[3..8] bracket the phases for hs_info when timed.
 int hs_plan_s::enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G,
-                       double2* H, double2* S, double2* Zw, double2* W2w, double2* AFw,
-                       cudaStream_t st, bool timed) {
+                       double2* H, double2* S, Workspace& w, cudaStream_t st, bool timed) {
   const int K = N_A * N_L;
   const int N_h = N_A - N_f;
+  if (w.N_G < N_G || w.n_fail < N_f) return HS_EINVAL;
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[3], st));
-  HS_CUDA_TRY(hs_launch_atoms_fp64(MZ, M2, fail_d, slot_d, A, B, ldAB, Zw, W2w, K, N_A, N_L,
+  HS_CUDA_TRY(hs_launch_atoms_fp64(MZ, M2, fail_d, slot_d, A, B, ldAB, w.Z, w.W2, K, N_A, N_L,
                                    N_G, st));
-  HS_CUDA_TRY(hs_launch_gather_af(A, ldAB, fail_list_d, N_f, N_L, N_G, AFw, st));
+  HS_CUDA_TRY(hs_launch_gather_af(A, ldAB, fail_list_d, N_f, N_L, N_G, w.AF, st));
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[4], st));
   SegList sS{}, sH{};
   sS.s[0] = Seg{A, A, nullptr, ldAB, ldAB, K};
   sS.s[1] = Seg{B, B, U, ldAB, ldAB, K};
   sS.n = 2;
   int n = 0;
-  sH.s[n++] = Seg{Zw, B, nullptr, K, ldAB, K};
-  sH.s[n++] = Seg{B, Zw, nullptr, ldAB, K, K};
-  if (N_h > 0) sH.s[n++] = Seg{W2w, W2w, nullptr, K, K, N_h * N_L};
-  if (N_f > 0) sH.s[n++] = Seg{AFw, W2w + (size_t)N_h * N_L, nullptr, N_f * N_L, K, N_f * N_L};
+  sH.s[n++] = Seg{w.Z, B, nullptr, K, ldAB, K};
+  sH.s[n++] = Seg{B, w.Z, nullptr, ldAB, K, K};
+  if (N_h > 0) sH.s[n++] = Seg{w.W2, w.W2, nullptr, K, K, N_h * N_L};
+  if (N_f > 0)
+    sH.s[n++] = Seg{w.AF, w.W2 + (size_t)N_h * N_L, nullptr, N_f * N_L, K, N_f * N_L};
   sH.n = n;
   if (precision == HS_FP64) {
     if (timed) HS_CUDA_TRY(cudaEventRecord(ev[5], st));
@@ -207,7 +239,7 @@ int hs_plan_s::enqueue(const double2* A, const double2* B, int ldAB, const doubl
     HS_CUDA_TRY(hs_launch_contract_fp64(sH, H, N_G, N_G, st));
     if (timed) HS_CUDA_TRY(cudaEventRecord(ev[7], st));
   } else {
-    int rc = split_enqueue(sS, sH, N_G, H, S, st, timed);
+    int rc = split_enqueue(sS, sH, N_G, H, S, w, st, timed);
     if (rc != HS_OK) return rc;
   }
   HS_CUDA_TRY(hs_launch_mirror(S, N_G, N_G, st));
@@ -239,17 +271,12 @@ void hs_plan_s::fill_info(hs_info* info, bool factored) {
     }
     return (double)ms;
   };
-  info->ms_factor = factored ? last_factor_ms : 0.0;
+  info->ms_factor = (factored || factor_pending_info) ? last_factor_ms : 0.0;
+  factor_pending_info = false;
   info->ms_atoms = el(3, 4);
-  if (precision == HS_FP64) {
-    info->ms_slice = 0.0;
-    info->ms_S = el(5, 6);
-    info->ms_H = el(6, 7);
-  } else {
-    info->ms_slice = el(4, 5);
-    info->ms_S = el(5, 6);
-    info->ms_H = el(6, 7);
-  }
+  info->ms_slice = precision == HS_FP64 ? 0.0 : el(4, 5);
+  info->ms_S = el(5, 6);
+  info->ms_H = el(6, 7);
   info->ms_finalize = el(7, 8);
   info->ms_total = el(3, 8) + info->ms_factor;
 }
@@ -263,6 +290,15 @@ static int check_args(hs_plan_t p, const void* A, const void* B, const void* T_A
   return HS_OK;
 }
 
+// The synchronous workspace: allocated on first use for N_G_max, regrown when
+// more atoms fail than it has room for.
+static int ensure_sync_ws(hs_plan_t p) {
+  if (p->ws.N_G == p->N_G_max && p->ws.n_fail >= p->N_f) return HS_OK;
+  HS_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  p->ws_free(p->ws, p->stream);
+  return p->ws_alloc(p->ws, p->N_G_max, p->N_f, p->stream, false);
+}
+
 extern "C" int hs_assemble(hs_plan_t p, const hs_z* A, const hs_z* B, const hs_z* T_AA,
                            const hs_z* T_AB, const hs_z* T_BB, const double* U, int N_A,
                            int N_L, int N_G, hs_z* H, hs_z* S, hs_info* info) {
@@ -272,13 +308,16 @@ extern "C" int hs_assemble(hs_plan_t p, const hs_z* A, const hs_z* B, const hs_z
   bool factored = false;
   if (!p->t_valid || p->tAA != (const void*)T_AA || p->tAB != (const void*)T_AB ||
       p->tBB != (const void*)T_BB) {
+    if (p->serve_busy()) return HS_EBUSY;
     rc = p->factor((const double2*)T_AA, (const double2*)T_AB, (const double2*)T_BB);
     if (rc) return rc;
     factored = true;
   }
+  rc = ensure_sync_ws(p);
+  if (rc) return rc;
   const int K = N_A * N_L;
-  rc = p->enqueue((const double2*)A, (const double2*)B, K, U, N_G, (double2*)H, (double2*)S, p->Z,
-                  p->W2, p->AF, p->stream, true);
+  rc = p->enqueue((const double2*)A, (const double2*)B, K, U, N_G, (double2*)H, (double2*)S, p->ws,
+                  p->stream, true);
   if (rc) return rc;
   HS_CUDA_TRY(cudaStreamSynchronize(p->stream));
   rc = p->check_device_error();
@@ -295,9 +334,9 @@ extern "C" int hs_assemble_host(hs_plan_t p, const hs_z* A, const hs_z* B, const
   std::lock_guard<std::mutex> lk(p->mu);
   const size_t K = (size_t)N_A * N_L;
   const size_t nT = (size_t)N_A * N_L * N_L;
-  const size_t sz[7] = {16 * K * p->N_G_max, 16 * K * p->N_G_max, 16 * nT * 3,
+  const size_t sz[6] = {16 * K * p->N_G_max, 16 * K * p->N_G_max, 16 * nT * 3,
                         8 * K, (size_t)16 * p->N_G_max * p->N_G_max,
-                        (size_t)16 * p->N_G_max * p->N_G_max, 0};
+                        (size_t)16 * p->N_G_max * p->N_G_max};
   for (int i = 0; i < 6; ++i)
     if (!p->stage[i] && cudaMalloc(&p->stage[i], sz[i]) != cudaSuccess) {
       cudaGetLastError();
@@ -316,6 +355,7 @@ extern "C" int hs_assemble_host(hs_plan_t p, const hs_z* A, const hs_z* B, const
   bool factored = false;
   if (!p->t_valid || p->host_tAA != (const void*)T_AA || p->host_tAB != (const void*)T_AB ||
       p->host_tBB != (const void*)T_BB) {
+    if (p->serve_busy()) return HS_EBUSY;
     HS_CUDA_TRY(cudaMemcpyAsync(dT, T_AA, 16 * nT, cudaMemcpyHostToDevice, st));
     HS_CUDA_TRY(cudaMemcpyAsync(dT + nT, T_AB, 16 * nT, cudaMemcpyHostToDevice, st));
     HS_CUDA_TRY(cudaMemcpyAsync(dT + 2 * nT, T_BB, 16 * nT, cudaMemcpyHostToDevice, st));
@@ -326,7 +366,9 @@ extern "C" int hs_assemble_host(hs_plan_t p, const hs_z* A, const hs_z* B, const
     p->host_tBB = T_BB;
     factored = true;
   }
-  rc = p->enqueue(dA, dB, (int)K, dU, N_G, dH, dS, p->Z, p->W2, p->AF, st, true);
+  rc = ensure_sync_ws(p);
+  if (rc) return rc;
+  rc = p->enqueue(dA, dB, (int)K, dU, N_G, dH, dS, p->ws, st, true);
   if (rc) return rc;
   HS_CUDA_TRY(cudaMemcpyAsync(H, dH, (size_t)16 * N_G * N_G, cudaMemcpyDeviceToHost, st));
   HS_CUDA_TRY(cudaMemcpyAsync(S, dS, (size_t)16 * N_G * N_G, cudaMemcpyDeviceToHost, st));

@@ -547,19 +547,16 @@ __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SlicePara
 // ------------------------------------------------------------------ host side
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                          &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    else
-      cudaGetLastError();
-  }
+      return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    cudaGetLastError();
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
 
@@ -578,101 +575,63 @@ bool encode_map(CUtensorMap* m, const uint16_t* base, int kpad, int rows_total) 
 
 }  // namespace
 
-// Slice buffers of one operand source (plain + optional rotated) and exponents.
-struct SliceBuf {
-  uint16_t* plain = nullptr;
-  uint16_t* rot = nullptr;
-  int* expo = nullptr;
-  size_t cap_rows_k = 0;  // allocated rows K capacity (complex)
-};
-
-enum { SRC_A = 0, SRC_UB, SRC_Z, SRC_B, SRC_Y, SRC_AF, SRC_X, NSRC };
-
-struct SplitWork {
-  SliceBuf buf[NSRC];
-  int rows_pad_max = 0;
-};
-
 static inline int kpad_of(int K) { return ((2 * K + KB - 1) / KB) * KB; }
 static inline int rows_pad_of(int N_G) { return ((N_G + ROWS_ALIGN - 1) / ROWS_ALIGN) * ROWS_ALIGN; }
 
-static size_t slicebuf_bytes(int s, int rows_pad, int K, bool rot) {
-  const size_t one = (size_t)s * rows_pad * kpad_of(K) * 2;
+// Complex rows (K) of each source and whether it needs the rotated copy.
+static void source_shape(int src, int K, int N_L, int n_fail, int& rows, bool& rot) {
+  rot = (src != SRC_AF);
+  rows = (src == SRC_AF || src == SRC_X) ? n_fail * N_L : K;
+}
+
+static size_t slicebuf_bytes(int s, int rows_pad, int Kc, bool rot) {
+  const size_t one = (size_t)s * rows_pad * kpad_of(Kc) * 2;
   return (rot ? 2 : 1) * one + sizeof(int) * rows_pad;
 }
 
-size_t hs_plan_s::split_bytes(int N_G) const {
+size_t hs_plan_s::split_ws_bytes(int N_G, int n_fail) const {
   if (precision != HS_SPLIT_BF16) return 0;
   const int K = N_A * N_L;
+  const int nf = n_fail > 0 ? n_fail : 1;
   const int rp = rows_pad_of(N_G);
-  // A, UB, Z, B, Y with rotated copies; A_f and X_f sized for every atom failing
-  return 5 * slicebuf_bytes(slices, rp, K, true) + slicebuf_bytes(slices, rp, K, false) +
-         slicebuf_bytes(slices, rp, K, true);
+  size_t b = 0;
+  for (int src = 0; src < NSRC; ++src) {
+    int rows;
+    bool rot;
+    source_shape(src, K, N_L, nf, rows, rot);
+    b += slicebuf_bytes(slices, rp, rows, rot);
+  }
+  return b;
 }
 
-static int alloc_slicebuf(SliceBuf& b, int s, int rows_pad, int K, bool rot) {
-  const size_t one = (size_t)s * rows_pad * kpad_of(K) * 2;
-  if (cudaMalloc((void**)&b.plain, one) != cudaSuccess) return HS_ENOMEM;
-  if (rot && cudaMalloc((void**)&b.rot, one) != cudaSuccess) return HS_ENOMEM;
-  if (cudaMalloc((void**)&b.expo, sizeof(int) * rows_pad) != cudaSuccess) return HS_ENOMEM;
-  b.cap_rows_k = (size_t)K;
-  return HS_OK;
-}
-
-static void free_slicebuf(SliceBuf& b) {
-  if (b.plain) cudaFree(b.plain);
-  if (b.rot) cudaFree(b.rot);
-  if (b.expo) cudaFree(b.expo);
-  b = SliceBuf{};
-}
-
-int hs_plan_s::split_alloc() {
+int hs_plan_s::split_ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st, bool async) {
   if (precision != HS_SPLIT_BF16) return HS_OK;
   if (!get_encode()) return HS_ECUDA;
-  split = new (std::nothrow) SplitWork();
-  if (!split) return HS_ENOMEM;
   const int K = N_A * N_L;
-  const int rp = rows_pad_of(N_G_max);
-  split->rows_pad_max = rp;
+  const int rp = rows_pad_of(N_G);
+  auto al = [&](void** ptr, size_t bytes) -> bool {
+    return (async ? hs_malloc_async(ptr, bytes, st, hs_serve_pool(this)) : cudaMalloc(ptr, bytes)) ==
+           cudaSuccess;
+  };
   for (int src = 0; src < NSRC; ++src) {
-    const bool rot = (src != SRC_AF);
-    // A_f / X_f buffers start small and grow with the number of failing atoms
-    const int Kc = (src == SRC_AF || src == SRC_X) ? N_L : K;
-    if (alloc_slicebuf(split->buf[src], slices, rp, Kc, rot) != HS_OK) {
-      cudaGetLastError();
-      return HS_ENOMEM;
-    }
+    int rows;
+    bool rot;
+    source_shape(src, K, N_L, n_fail, rows, rot);
+    const size_t one = (size_t)slices * rp * kpad_of(rows) * 2;
+    if (!al((void**)&w.sb[src].plain, one)) return HS_ENOMEM;
+    if (rot && !al((void**)&w.sb[src].rot, one)) return HS_ENOMEM;
+    if (!al((void**)&w.sb[src].expo, sizeof(int) * rp)) return HS_ENOMEM;
   }
   return HS_OK;
 }
 
-void hs_plan_s::split_release() {
-  if (!split) return;
-  for (auto& b : split->buf) free_slicebuf(b);
-  delete split;
-  split = nullptr;
-}
-
 int hs_plan_s::split_enqueue(const SegList& sS, const SegList& sH, int N_G, double2* H,
-                             double2* S, cudaStream_t st, bool timed) {
-  if (!split) return HS_ENOTSUP;
+                             double2* S, Workspace& w, cudaStream_t st, bool timed) {
   const int K = N_A * N_L;
   const int N_h = N_A - N_f;
   const int s = slices;
   const int rp = rows_pad_of(N_G);
-  // grow the A_f / X_f slice buffers with the number of failing atoms
-  for (int src : {SRC_AF, SRC_X}) {
-    SliceBuf& b = split->buf[src];
-    const size_t need = (size_t)(N_f > 0 ? N_f : 1) * N_L;
-    if (need > b.cap_rows_k) {
-      HS_CUDA_TRY(cudaStreamSynchronize(st));
-      free_slicebuf(b);
-      if (alloc_slicebuf(b, s, split->rows_pad_max, (int)need, src != SRC_AF) != HS_OK) {
-        cudaGetLastError();
-        return HS_ENOMEM;
-      }
-    }
-  }
+  if (rows_pad_of(w.N_G) < rp || w.n_fail < N_f || !w.sb[SRC_A].plain) return HS_EINVAL;
   // sources: sS.s[0] = (A, A), sS.s[1] = (B, B, U), sH.s[0] = (Z, B), then (Y, Y), (A_f, X_f)
   const Seg& sA = sS.s[0];
   const Seg& sUB = sS.s[1];
@@ -697,7 +656,7 @@ int hs_plan_s::split_enqueue(const SegList& sS, const SegList& sH, int N_G, doub
   sp.rows_pad = rp;
   int nj = 0;
   auto job = [&](int src, const double2* X, int ldX, int Kr, const double* u) {
-    SliceBuf& b = split->buf[src];
+    SliceBuf& b = w.sb[src];
     sp.job[nj++] = SliceJob{X, u, b.plain, b.rot, b.expo, ldX, Kr, kpad_of(Kr)};
   };
   job(SRC_A, sA.L, sA.ldL, K, nullptr);
@@ -718,8 +677,9 @@ int hs_plan_s::split_enqueue(const SegList& sS, const SegList& sH, int N_G, doub
   std::memset(&P, 0, sizeof(P));
   int map_of[NSRC][2];
   int nm = 0;
+  // a slice array's rows: rp per slice (this call's padding, within capacity)
   auto add_map = [&](int src, int Kr) -> int {
-    SliceBuf& b = split->buf[src];
+    SliceBuf& b = w.sb[src];
     map_of[src][0] = nm;
     if (!encode_map(&P.maps[nm++], b.plain, kpad_of(Kr), s * rp)) return HS_ECUDA;
     if (b.rot) {
@@ -763,8 +723,8 @@ int hs_plan_s::split_enqueue(const SegList& sS, const SegList& sH, int N_G, doub
     g.mR = map_of[srcR][0];
     g.mRr = map_of[srcR][1];
     g.kblocks = kpad_of(Kr) / KB;
-    g.eL = split->buf[srcL].expo;
-    g.eR = split->buf[srcR].expo;
+    g.eL = w.sb[srcL].expo;
+    g.eR = w.sb[srcR].expo;
     return g;
   };
   // S = A^H A + (UB)^H (UB)

@@ -17,8 +17,37 @@ constexpr int kMaxNL = 168;       // packed lower triangle of T^AA fits in 227 K
 constexpr int kDefaultSlices = 5;
 constexpr int kMaxSlices = 7;  // 7 + 9*(s-1) bits must fit an int64 digit word
 
-struct SplitWork;   // k_split.cu
+// Slice buffers of one operand source: s BF16 arrays [p][rows_pad][kpad] of
+// (re, im) pairs, optionally the same for (im, -re) pairs, and one exponent
+// per row (= column of the operand).
+struct SliceBuf {
+  uint16_t* plain = nullptr;
+  uint16_t* rot = nullptr;
+  int* expo = nullptr;
+};
+// Operand sources of the two contractions.
+enum { SRC_A = 0, SRC_UB, SRC_Z, SRC_B, SRC_Y, SRC_AF, SRC_X, NSRC };
+
+// Per-k-point device workspace.  The synchronous path owns one sized for
+// N_G_max; every admitted serving request gets its own, sized exactly.
+struct Workspace {
+  double2* Z = nullptr;   // K x N_G (Z_a stacked)
+  double2* W2 = nullptr;  // K x N_G (Y_HPD rows, then X_notHPD rows)
+  double2* AF = nullptr;  // (N_f N_L) x N_G (A rows of failing atoms)
+  int N_G = 0;            // capacity in columns
+  int n_fail = 0;         // capacity of AF and of the A_f / X_f slices, in atoms
+  SliceBuf sb[NSRC];      // split form only
+  bool async = false;     // allocated with cudaMallocAsync (serving)
+};
+
 struct ServeState;  // serve.cu
+struct hs_plan_s;
+// Stream-ordered pool for serving workspaces (null before the first hs_submit).
+cudaMemPool_t hs_serve_pool(hs_plan_s* p);
+// cudaMallocAsync from the serving pool when there is one.
+inline cudaError_t hs_malloc_async(void** ptr, size_t bytes, cudaStream_t st, cudaMemPool_t pool) {
+  return pool ? cudaMallocFromPoolAsync(ptr, bytes, pool, st) : cudaMallocAsync(ptr, bytes, st);
+}
 
 struct hs_plan_s {
   std::mutex mu;
@@ -27,11 +56,7 @@ struct hs_plan_s {
   size_t budget = 0;
   cudaStream_t stream = nullptr;
 
-  // per-k-point workspace (FP64)
-  double2* Z = nullptr;   // K x N_G_max   (Z_a stacked)
-  double2* W2 = nullptr;  // K x N_G_max   (Y_HPD rows, then X_notHPD rows)
-  double2* AF = nullptr;  // (N_f N_L) x N_G_max  (A_notHPD)
-  int af_atoms = 0;
+  Workspace ws;  // synchronous calls
 
   // factor cache (k-independent)
   double2* M2 = nullptr;  // N_A x N_L x N_L : L_a^H or T^AA_a
@@ -45,26 +70,29 @@ struct hs_plan_s {
   const void *host_tAA = nullptr, *host_tAB = nullptr, *host_tBB = nullptr;
   bool t_valid = false;
   double last_factor_ms = 0.0;
+  bool factor_pending_info = false;  // hs_set_t ran since the last hs_assemble
 
   int* err_d = nullptr;  // device error word (bounded waits)
   cudaEvent_t ev[10] = {};
   void* stage[6] = {};   // host-call staging: A, B, T, U, H, S
 
-  SplitWork* split = nullptr;
   ServeState* serve = nullptr;
 
-  size_t workspace_bytes(int N_G) const;
+  // workspace sizing and allocation (hs_api.cu / k_split.cu)
+  size_t ws_bytes(int N_G, int n_fail) const;      // exact bytes of one workspace
+  size_t split_ws_bytes(int N_G, int n_fail) const;
+  int ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st, bool async);
+  int split_ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st, bool async);
+  void ws_free(Workspace& w, cudaStream_t st);
   size_t fixed_bytes() const;
-  size_t split_bytes(int N_G) const;
-  int split_alloc();
-  void split_release();
   void release();
   int factor(const double2* T_AA, const double2* T_AB, const double2* T_BB);
   int enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G, double2* H,
-              double2* S, double2* Zw, double2* W2w, double2* AFw, cudaStream_t st, bool timed);
+              double2* S, Workspace& w, cudaStream_t st, bool timed);
   int split_enqueue(const SegList& sS, const SegList& sH, int N_G, double2* H, double2* S,
-                    cudaStream_t st, bool timed);
+                    Workspace& w, cudaStream_t st, bool timed);
   int check_device_error();
   void fill_info(hs_info* info, bool factored);
+  bool serve_busy();
   void serve_shutdown();
 };

@@ -34,7 +34,9 @@ PRECISIONS = {"fp64": HS_FP64, "split_bf16": HS_SPLIT_BF16}
 class hs_info(C.Structure):
     _fields_ = [("n_fallback", C.c_int), ("slices", C.c_int), ("ms_total", C.c_double),
                 ("ms_factor", C.c_double), ("ms_atoms", C.c_double), ("ms_slice", C.c_double),
-                ("ms_S", C.c_double), ("ms_H", C.c_double), ("ms_finalize", C.c_double)]
+                ("ms_S", C.c_double), ("ms_H", C.c_double), ("ms_finalize", C.c_double),
+                ("ms_queue", C.c_double), ("ms_latency", C.c_double),
+                ("inflight_bytes", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
