@@ -263,8 +263,12 @@ def main():
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "work": "Algorithm 1 flops of H1+H2+H3 (FP64 DFMA)",
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
-    launches_per_step = 2 + 1 + (1 if N_f else 0) + 2 + 2 + (1 if args.precision ==
-                                                                 "split_bf16" else 0)
+    # our kernels per step: factor (Cholesky, MZ prep [+ 2 operator slicers]), per-atom
+    # products (+ A_f gather), [2 slicers], S and H contractions, 2 mirrors
+    if args.precision == "split_bf16":
+        launches_per_step = 4 + 1 + (1 if N_f else 0) + 2 + 2 + 2
+    else:
+        launches_per_step = 2 + 1 + (1 if N_f else 0) + 2 + 2
 
     # ---------------- plain FP64 GPU form, same run
     fp64 = None

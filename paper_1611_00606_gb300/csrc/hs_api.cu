@@ -45,7 +45,8 @@ size_t hs_plan_s::ws_bytes(int N_G, int n_fail) const {
 }
 
 size_t hs_plan_s::fixed_bytes() const {
-  return (size_t)16 * N_A * N_L * N_L * 3 + (size_t)sizeof(int) * (3 * N_A + 16);
+  return (size_t)16 * N_A * N_L * N_L * 3 + (size_t)sizeof(int) * (3 * N_A + 16) +
+         split_fixed_bytes();
 }
 
 static void free_ptr(void*& p) {
@@ -105,6 +106,7 @@ void hs_plan_s::release() {
   free_ptr((void*&)slot_d);
   free_ptr((void*&)fail_list_d);
   free_ptr((void*&)err_d);
+  split_plan_release();
   for (auto& p : stage) free_ptr(p);
   for (auto& e : ev)
     if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -150,6 +152,7 @@ extern "C" int hs_plan(hs_plan_t* out, int N_A, int N_L, int N_G_max, int precis
   ok = ok && alloc((void**)&p->slot_d, sizeof(int) * N_A);
   ok = ok && alloc((void**)&p->fail_list_d, sizeof(int) * N_A);
   ok = ok && alloc((void**)&p->err_d, sizeof(int) * 16);
+  ok = ok && (p->split_plan_alloc() == HS_OK);
   for (auto& e : p->ev) ok = ok && (cudaEventCreate(&e) == cudaSuccess);
   if (!ok) {
     cudaGetLastError();
@@ -171,6 +174,8 @@ extern "C" size_t hs_footprint(hs_plan_t p, int N_G) {
 int hs_plan_s::factor(const double2* T_AA, const double2* T_AB, const double2* T_BB) {
   HS_CUDA_TRY(cudaEventRecord(ev[1], stream));
   HS_CUDA_TRY(hs_launch_factor(T_AA, T_AB, T_BB, N_A, N_L, M2, MZ, fail_d, stream));
+  int rc = split_factor(stream);
+  if (rc != HS_OK) return rc;
   fail_h.assign(N_A, 0);
   HS_CUDA_TRY(cudaMemcpyAsync(fail_h.data(), fail_d, sizeof(int) * N_A, cudaMemcpyDeviceToHost,
                               stream));
@@ -217,30 +222,30 @@ int hs_plan_s::enqueue(const double2* A, const double2* B, int ldAB, const doubl
   const int N_h = N_A - N_f;
   if (w.N_G < N_G || w.n_fail < N_f) return HS_EINVAL;
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[3], st));
-  HS_CUDA_TRY(hs_launch_atoms_fp64(MZ, M2, fail_d, slot_d, A, B, ldAB, w.Z, w.W2, K, N_A, N_L,
-                                   N_G, st));
-  HS_CUDA_TRY(hs_launch_gather_af(A, ldAB, fail_list_d, N_f, N_L, N_G, w.AF, st));
-  if (timed) HS_CUDA_TRY(cudaEventRecord(ev[4], st));
-  SegList sS{}, sH{};
-  sS.s[0] = Seg{A, A, nullptr, ldAB, ldAB, K};
-  sS.s[1] = Seg{B, B, U, ldAB, ldAB, K};
-  sS.n = 2;
-  int n = 0;
-  sH.s[n++] = Seg{w.Z, B, nullptr, K, ldAB, K};
-  sH.s[n++] = Seg{B, w.Z, nullptr, ldAB, K, K};
-  if (N_h > 0) sH.s[n++] = Seg{w.W2, w.W2, nullptr, K, K, N_h * N_L};
-  if (N_f > 0)
-    sH.s[n++] = Seg{w.AF, w.W2 + (size_t)N_h * N_L, nullptr, N_f * N_L, K, N_f * N_L};
-  sH.n = n;
-  if (precision == HS_FP64) {
+  if (precision == HS_SPLIT_BF16) {
+    int rc = split_enqueue(A, B, ldAB, U, N_G, H, S, w, st, timed);
+    if (rc != HS_OK) return rc;
+  } else {
+    HS_CUDA_TRY(hs_launch_atoms_fp64(MZ, M2, fail_d, slot_d, A, B, ldAB, w.Z, w.W2, K, N_A, N_L,
+                                     N_G, st));
+    HS_CUDA_TRY(hs_launch_gather_af(A, ldAB, fail_list_d, N_f, N_L, N_G, w.AF, st));
+    if (timed) HS_CUDA_TRY(cudaEventRecord(ev[4], st));
+    SegList sS{}, sH{};
+    sS.s[0] = Seg{A, A, nullptr, ldAB, ldAB, K};
+    sS.s[1] = Seg{B, B, U, ldAB, ldAB, K};
+    sS.n = 2;
+    int n = 0;
+    sH.s[n++] = Seg{w.Z, B, nullptr, K, ldAB, K};
+    sH.s[n++] = Seg{B, w.Z, nullptr, ldAB, K, K};
+    if (N_h > 0) sH.s[n++] = Seg{w.W2, w.W2, nullptr, K, K, N_h * N_L};
+    if (N_f > 0)
+      sH.s[n++] = Seg{w.AF, w.W2 + (size_t)N_h * N_L, nullptr, N_f * N_L, K, N_f * N_L};
+    sH.n = n;
     if (timed) HS_CUDA_TRY(cudaEventRecord(ev[5], st));
     HS_CUDA_TRY(hs_launch_contract_fp64(sS, S, N_G, N_G, st));
     if (timed) HS_CUDA_TRY(cudaEventRecord(ev[6], st));
     HS_CUDA_TRY(hs_launch_contract_fp64(sH, H, N_G, N_G, st));
     if (timed) HS_CUDA_TRY(cudaEventRecord(ev[7], st));
-  } else {
-    int rc = split_enqueue(sS, sH, N_G, H, S, w, st, timed);
-    if (rc != HS_OK) return rc;
   }
   HS_CUDA_TRY(hs_launch_mirror(S, N_G, N_G, st));
   HS_CUDA_TRY(hs_launch_mirror(H, N_G, N_G, st));
@@ -273,8 +278,13 @@ void hs_plan_s::fill_info(hs_info* info, bool factored) {
   };
   info->ms_factor = (factored || factor_pending_info) ? last_factor_ms : 0.0;
   factor_pending_info = false;
-  info->ms_atoms = el(3, 4);
-  info->ms_slice = precision == HS_FP64 ? 0.0 : el(4, 5);
+  if (precision == HS_FP64) {
+    info->ms_atoms = el(3, 4);
+    info->ms_slice = 0.0;
+  } else {  // slice inputs [3, 9], per-atom products [9, 4], slice outputs [4, 5]
+    info->ms_atoms = el(9, 4);
+    info->ms_slice = el(3, 9) + el(4, 5);
+  }
   info->ms_S = el(5, 6);
   info->ms_H = el(6, 7);
   info->ms_finalize = el(7, 8);

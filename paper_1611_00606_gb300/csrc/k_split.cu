@@ -192,13 +192,42 @@ __device__ __forceinline__ void drain_cols(uint32_t taddr, int s, float rsc, flo
   }
 }
 
-// ------------------------------------------------------------------ contraction
+// ------------------------------------------------------------------ slice-GEMM kernel
+//
+// One kernel body serves two work decompositions (template MODE):
+//  * MODE_CONTRACT: a 128 x 64 complex lower-triangle tile of S or H; K runs
+//    over the contraction's segments (L', R', R'' slice arrays).
+//  * MODE_ATOMS: the per-atom products of Algorithm 1's loops,
+//      Z_a = [T^BA_a | 1/2 T^BB_a] [A_a; B_a],  W2_slot(a) = M2_a A_a,
+//    as D[g][n] = sum_k X'[g][k] Op_a[n][k] with X' the coefficient slices of
+//    atom a (rows g) and Op_a the sliced real form of the per-atom operator
+//    (row n = 2L + c gives Re/Im of output row L).  Tile: 128 g x 128 n.
+// Both share the TMA -> smem ring, the tcgen05 issue loop, the exact-window
+// TMEM accumulators and the double-float drain; they differ in where each
+// K segment's tiles come from, which exponents scale the drain, and the
+// epilogue.
+
+enum { MODE_CONTRACT = 0, MODE_ATOMS = 1 };
 
 struct SplitSeg {
   int mL, mR, mRr;  // tensor maps of L', R', R''
   int kblocks;      // stages of KB real K
   const int* eL;    // exponents of the L source columns
   const int* eR;    // exponents of the R source columns
+};
+
+struct AtomsArgs {
+  int mA, mB;             // coefficient slice maps (plain)
+  int mOp[2];             // operator slice maps: [0] Z job, [1] W2 job
+  const int* eA;          // column exponents of A, B
+  const int* eB;
+  const int* eOp[2];      // operator row exponents [a][n_pad]
+  const int* slot;        // W2 slot of each atom
+  double2* Z;             // outputs, column-major, leading dimension ld
+  double2* W2;
+  int ld;
+  int N_A, N_L, P;        // P: padded real K of one atom block (multiple of KB)
+  int n_pad, ntile, ngblk;
 };
 
 struct __align__(64) SplitParams {
@@ -208,13 +237,100 @@ struct __align__(64) SplitParams {
   int s;          // slices
   int n_stage;    // pipeline depth
   int N_G, ldC, nbj;
-  int rows_pad;   // slice p of an operand starts at row p * rows_pad
+  int rows_pad;   // slice p of a coefficient-side array starts at row p * rows_pad
   double2* C;
   int* err;
+  AtomsArgs at;
 };
 
-__global__ void __launch_bounds__(NUM_THREADS, 1)
-    k_contract_split(const __grid_constant__ SplitParams P) {
+// Where one K segment of this CTA's tile lives.
+struct SegInfo {
+  const CUtensorMap* mL;
+  const CUtensorMap* mR1;
+  const CUtensorMap* mR2;
+  int xL, yL, ysL;          // L side: x base, row base (slice 0), rows per slice
+  int xR, yR1, yR2, ysR;    // R side: x base, row bases of the two 64-row boxes, rows per slice
+  int kblocks;
+  const int* eRow;          // indexed by the tile's absolute row
+  const int* eC0;           // column exponents of TMEM columns [0, 64) (+ column in strip)
+  const int* eC1;           // columns [64, 128)
+};
+
+struct TileId {
+  int i0, j0;      // CONTRACT: row / column origin
+  int a, job, n0;  // ATOMS: atom, job (0: Z, 1: W2), operator row origin (i0 = g origin)
+  int nseg;
+};
+
+template <int MODE>
+__device__ __forceinline__ TileId decode_tile(const SplitParams& P) {
+  TileId t{};
+  if (MODE == MODE_CONTRACT) {
+    int b = blockIdx.x, bi = 0;
+    for (;;) {
+      const int n = min(2 * bi + 2, P.nbj);
+      if (b < n) break;
+      b -= n;
+      ++bi;
+    }
+    t.i0 = bi * BM;
+    t.j0 = b * BNC;
+    t.nseg = P.nseg;
+  } else {
+    int b = blockIdx.x;
+    const int gb = b % P.at.ngblk;
+    b /= P.at.ngblk;
+    const int nt = b % P.at.ntile;
+    b /= P.at.ntile;
+    t.job = b & 1;
+    t.a = b >> 1;
+    t.i0 = gb * BM;
+    t.n0 = nt * BN;
+    t.nseg = t.job == 0 ? 2 : 1;
+  }
+  return t;
+}
+
+template <int MODE>
+__device__ __forceinline__ SegInfo seg_info(const SplitParams& P, const TileId& t, int sg) {
+  SegInfo si;
+  if (MODE == MODE_CONTRACT) {
+    const SplitSeg& S = P.seg[sg];
+    si.mL = &P.maps[S.mL];
+    si.mR1 = &P.maps[S.mR];
+    si.mR2 = &P.maps[S.mRr];
+    si.xL = 0;
+    si.yL = t.i0;
+    si.ysL = P.rows_pad;
+    si.xR = 0;
+    si.yR1 = t.j0;
+    si.yR2 = t.j0;
+    si.ysR = P.rows_pad;
+    si.kblocks = S.kblocks;
+    si.eRow = S.eL;
+    si.eC0 = S.eR + t.j0;
+    si.eC1 = S.eR + t.j0;
+  } else {
+    const AtomsArgs& A = P.at;
+    si.mL = &P.maps[sg == 0 ? A.mA : A.mB];
+    si.mR1 = si.mR2 = &P.maps[A.mOp[t.job]];
+    si.xL = t.a * A.P;
+    si.yL = t.i0;
+    si.ysL = P.rows_pad;
+    si.xR = sg * A.P;  // Z operator: A part in [0, P), B part in [P, 2P)
+    si.yR1 = t.a * P.s * A.n_pad + t.n0;
+    si.yR2 = si.yR1 + 64;
+    si.ysR = A.n_pad;
+    si.kblocks = A.P / KB;
+    si.eRow = sg == 0 ? A.eA : A.eB;
+    si.eC0 = A.eOp[t.job] + t.a * A.n_pad + t.n0;
+    si.eC1 = si.eC0 + 64;
+  }
+  return si;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_constant__ SplitParams P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -230,16 +346,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
-  // lower-triangle tile of 128 x 64: row block bi, column block bj <= 2 bi + 1
-  int t = blockIdx.x, bi = 0;
-  for (;;) {
-    const int n = min(2 * bi + 2, P.nbj);
-    if (t < n) break;
-    t -= n;
-    ++bi;
-  }
-  const int bj = t;
-  const int i0 = bi * BM, j0 = bj * BNC;
+  const TileId T = decode_tile<MODE>(P);
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < NS; ++i) {
@@ -254,10 +361,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 0 && lane == 0)
-    for (int sg = 0; sg < P.nseg; ++sg) {
-      prefetch_map(&P.maps[P.seg[sg].mL]);
-      prefetch_map(&P.maps[P.seg[sg].mR]);
-      prefetch_map(&P.maps[P.seg[sg].mRr]);
+    for (int sg = 0; sg < T.nseg; ++sg) {
+      const SegInfo si = seg_info<MODE>(P, T, sg);
+      prefetch_map(si.mL);
+      prefetch_map(si.mR1);
+      prefetch_map(si.mR2);
     }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
@@ -278,12 +386,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t armed = 0;        // bit i: slot i was armed at least once
       uint32_t armed_par = 0;    // bit i: parity of the last armed phase of slot i
       bool ok = true;
-      for (int sg = 0; sg < P.nseg && ok; ++sg) {
-        const SplitSeg S = P.seg[sg];
-        const CUtensorMap* mL = &P.maps[S.mL];
-        const CUtensorMap* mR = &P.maps[S.mR];
-        const CUtensorMap* mRr = &P.maps[S.mRr];
-        for (int kb = 0; kb < S.kblocks; ++kb) {
+      for (int sg = 0; sg < T.nseg && ok; ++sg) {
+        const SegInfo si = seg_info<MODE>(P, T, sg);
+        for (int kb = 0; kb < si.kblocks; ++kb) {
           if (!mbar_wait(&empty[slot], phase ^ 1u, abort_flag)) {
             ok = false;
             break;
@@ -293,13 +398,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           armed_par = (armed_par & ~(1u << slot)) | (phase << slot);
           const uint32_t sa = smem_u32(smem + slot * stage_bytes);
           const uint32_t sb = sa + a_bytes;
-          const int x = kb * KB;
+          const int xl = si.xL + kb * KB, xr = si.xR + kb * KB;
           for (int p = 0; p < s; ++p) {
-            const int yr = p * P.rows_pad;
-            tma_load_2d(sa + p * 2 * TILE_BYTES, mL, x, yr + i0, &full[slot]);
-            tma_load_2d(sa + p * 2 * TILE_BYTES + TILE_BYTES, mL, x, yr + i0 + 64, &full[slot]);
-            tma_load_2d(sb + p * 2 * TILE_BYTES, mR, x, yr + j0, &full[slot]);
-            tma_load_2d(sb + p * 2 * TILE_BYTES + TILE_BYTES, mRr, x, yr + j0, &full[slot]);
+            const int yl = si.yL + p * si.ysL;
+            tma_load_2d(sa + p * 2 * TILE_BYTES, si.mL, xl, yl, &full[slot]);
+            tma_load_2d(sa + p * 2 * TILE_BYTES + TILE_BYTES, si.mL, xl, yl + 64, &full[slot]);
+            tma_load_2d(sb + p * 2 * TILE_BYTES, si.mR1, xr, si.yR1 + p * si.ysR, &full[slot]);
+            tma_load_2d(sb + p * 2 * TILE_BYTES + TILE_BYTES, si.mR2, xr, si.yR2 + p * si.ysR,
+                        &full[slot]);
           }
           if (++slot == NS) {
             slot = 0;
@@ -326,8 +432,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       uint32_t phase = 0;
       int nwin = 0;
       bool ok = true;
-      for (int sg = 0; sg < P.nseg && ok; ++sg) {
-        const int kbn = P.seg[sg].kblocks;
+      for (int sg = 0; sg < T.nseg && ok; ++sg) {
+        const int kbn = seg_info<MODE>(P, T, sg).kblocks;
         for (int w0 = 0; w0 < kbn && ok; w0 += WIN) {
           if (nwin > 0 && !mbar_wait(acc_empty, (uint32_t)(nwin - 1) & 1u, abort_flag)) {
             ok = false;
@@ -377,26 +483,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   } else {
     // ---------------- drain warps 2..9: TMEM -> double-float accumulators
     const int q4 = warp & 3;        // TMEM lane quarter this warp may access
-    const int h = (warp - 2) >> 2;  // column half
-    const int row = i0 + 32 * q4 + lane;
+    const int h = (warp - 2) >> 2;  // 32-column half of each 64-column strip
+    const int row = T.i0 + 32 * q4 + lane;
     const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16);
-    float hr[32], lr[32], hi_[32], li[32];
+    float h0[32], l0[32], h1[32], l1[32];  // strip 0 (TMEM cols < 64), strip 1
 #pragma unroll
-    for (int c = 0; c < 32; ++c) hr[c] = lr[c] = hi_[c] = li[c] = 0.f;
+    for (int c = 0; c < 32; ++c) h0[c] = l0[c] = h1[c] = l1[c] = 0.f;
     int nwin = 0;
     bool ok = true;
-    for (int sg = 0; sg < P.nseg && ok; ++sg) {
-      const SplitSeg S = P.seg[sg];
-      const float rsc = pow2f(S.eL[row]);
-      const float csc = pow2f(S.eR[j0 + 32 * h + lane]);  // lane c: column c's scale
-      for (int w0 = 0; w0 < S.kblocks; w0 += WIN) {
+    for (int sg = 0; sg < T.nseg && ok; ++sg) {
+      const SegInfo si = seg_info<MODE>(P, T, sg);
+      const float rsc = pow2f(si.eRow[row]);
+      const float csc0 = pow2f(si.eC0[32 * h + lane]);  // lane c: column c's scale
+      const float csc1 = pow2f(si.eC1[32 * h + lane]);
+      for (int w0 = 0; w0 < si.kblocks; w0 += WIN) {
         if (!mbar_wait(acc_full, (uint32_t)nwin & 1u, abort_flag)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        drain_cols(tl + (uint32_t)(32 * h), s, rsc, csc, hr, lr);            // Re
-        drain_cols(tl + (uint32_t)(BNC + 32 * h), s, rsc, csc, hi_, li);     // Im
+        drain_cols(tl + (uint32_t)(32 * h), s, rsc, csc0, h0, l0);
+        drain_cols(tl + (uint32_t)(BNC + 32 * h), s, rsc, csc1, h1, l1);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acc_empty);
@@ -406,13 +513,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     if (!ok) {
       atomicExch(P.err, 3);
       *abort_flag = 1;
-    } else if (row < P.N_G) {
+    } else if (MODE == MODE_CONTRACT) {
+      if (row < P.N_G) {
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const int j = j0 + 32 * h + c;
-        if (j < P.N_G)
-          P.C[row + (size_t)j * P.ldC] =
-              make_double2((double)hr[c] + (double)lr[c], (double)hi_[c] + (double)li[c]);
+        for (int c = 0; c < 32; ++c) {
+          const int j = T.j0 + 32 * h + c;
+          if (j < P.N_G)
+            P.C[row + (size_t)j * P.ldC] =
+                make_double2((double)h0[c] + (double)l0[c], (double)h1[c] + (double)l1[c]);
+        }
+      }
+    } else if (row < P.N_G) {
+      const AtomsArgs& A = P.at;
+      double2* out = (T.job == 0 ? A.Z + (size_t)T.a * A.N_L
+                                 : A.W2 + (size_t)A.slot[T.a] * A.N_L) + (size_t)row * A.ld;
+      const int L0 = (T.n0 >> 1) + 16 * h;  // first output row of strip 0 for this warp
+#pragma unroll
+      for (int c = 0; c < 32; c += 2) {
+        const int L = L0 + (c >> 1);
+        if (L < A.N_L)
+          out[L] = make_double2((double)h0[c] + (double)l0[c],
+                                (double)h0[c + 1] + (double)l0[c + 1]);
+        const int L1 = L + 32;
+        if (L1 < A.N_L)
+          out[L1] = make_double2((double)h1[c] + (double)l1[c],
+                                 (double)h1[c + 1] + (double)l1[c + 1]);
       }
     }
   }
@@ -425,19 +550,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
 }
 
-// ------------------------------------------------------------------ slicer
+// ------------------------------------------------------------------ slicers
 
+// Padded real-K layout shared by every slice array: complex row k of a source
+// with blocks of N_L rows (atoms or slots) sits at real position
+// (k / N_L) * P + 2 (k % N_L) (+1 for the imaginary part), P = roundup(2 N_L, 16);
+// the gaps hold zeros.  Every atom block therefore starts on a 32-byte TMA
+// boundary, which the per-atom products need.
 struct SliceJob {
-  const double2* X;  // source: K x N_G complex, column-major, ld ldX
+  const double2* X;  // source: nblk * N_L complex rows x N_G, column-major, ld ldX
   const double* u;   // optional real row weight (the U norms), may be null
-  uint16_t* plain;   // [s][rows_pad][kpad] BF16 slices of (re, im) pairs
+  uint16_t* plain;   // [s][rows_pad][nblk * P] BF16 slices of (re, im) pairs
   uint16_t* rot;     // same for (im, -re) pairs, may be null
   int* expo;         // [rows_pad] column exponents
-  int ldX, K, kpad;
+  int ldX, nblk;
 };
 struct SliceParams {
   SliceJob job[kMaxJobs];
-  int s, N_G, rows_pad;
+  int s, N_G, rows_pad, N_L, P;
 };
 
 // Balanced base-512 digits of round(x * 2^(9(s-1) - E)); d[0] is the leading one.
@@ -471,26 +601,70 @@ __device__ __forceinline__ uint16_t bf16_bits(float f) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(f));
 }
 
+// Exponent E with max / 2^E in [64, 128) (0 for an all-zero or non-finite max).
+__device__ __forceinline__ int slice_exponent(double mm) {
+  int e = 0;
+  if (mm > 0.0 && isfinite(mm)) {
+    frexp(mm, &e);
+    return e - 7;
+  }
+  return 0;
+}
+
+// Write the s slices of one complex entry (re, im): plain (re, im) and rotated (im, -re).
+__device__ __forceinline__ void put_slices(double2 v, bool zero, int E, int s, uint16_t* plain,
+                                           uint16_t* rot, size_t slice_elems, size_t off) {
+  int dr[kMaxSlices], di[kMaxSlices];
+  const bool bad = !zero && !(isfinite(v.x) && isfinite(v.y));
+  if (!zero) {
+    digits_of(v.x, E, s, dr);
+    digits_of(v.y, E, s, di);
+  } else {
+#pragma unroll
+    for (int p = 0; p < kMaxSlices; ++p) dr[p] = di[p] = 0;
+  }
+#pragma unroll
+  for (int p = 0; p < kMaxSlices; ++p) {
+    if (p < s) {
+      const float sc = __int_as_float((127 - 9 * p) << 23);  // 2^{-9p}
+      uint32_t pl, rt;
+      if (bad) {
+        pl = rt = 0x7FC07FC0u;  // NaN pair: propagates through the MMA
+      } else {
+        pl = (uint32_t)bf16_bits((float)dr[p] * sc) |
+             ((uint32_t)bf16_bits((float)di[p] * sc) << 16);
+        rt = (uint32_t)bf16_bits((float)di[p] * sc) |
+             ((uint32_t)bf16_bits((float)(-dr[p]) * sc) << 16);
+      }
+      *(uint32_t*)(plain + p * slice_elems + off) = pl;
+      if (rot) *(uint32_t*)(rot + p * slice_elems + off) = rt;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SliceParams P) {
   const SliceJob J = P.job[blockIdx.y];
   const int g = blockIdx.x;
   const int s = P.s;
-  const size_t slice_elems = (size_t)P.rows_pad * J.kpad;
+  const int kpad = J.nblk * P.P;
+  const size_t slice_elems = (size_t)P.rows_pad * kpad;
+  const int hp = P.P / 2;  // complex positions per block
   __shared__ double red[32];
   __shared__ int s_E;
-  const int kc = J.kpad / 2;  // complex entries per padded row
+  const int kc = kpad / 2;  // complex positions per padded row
   if (g >= P.N_G) {
     for (int k = threadIdx.x; k < kc; k += blockDim.x)
       for (int p = 0; p < s; ++p) {
-        ((uint32_t*)(J.plain + p * slice_elems + (size_t)g * J.kpad))[k] = 0u;
-        if (J.rot) ((uint32_t*)(J.rot + p * slice_elems + (size_t)g * J.kpad))[k] = 0u;
+        ((uint32_t*)(J.plain + p * slice_elems + (size_t)g * kpad))[k] = 0u;
+        if (J.rot) ((uint32_t*)(J.rot + p * slice_elems + (size_t)g * kpad))[k] = 0u;
       }
     if (threadIdx.x == 0) J.expo[g] = 0;
     return;
   }
   const double2* col = J.X + (size_t)g * J.ldX;
+  const int K = J.nblk * P.N_L;
   double m = 0.0;
-  for (int k = threadIdx.x; k < J.K; k += blockDim.x) {
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double2 v = col[k];
     const double w = J.u ? fabs(J.u[k]) : 1.0;
     m = fmax(m, fmax(fabs(v.x), fabs(v.y)) * w);
@@ -501,46 +675,72 @@ __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SlicePara
   if (threadIdx.x == 0) {
     double mm = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = fmax(mm, red[i]);
-    int e = 0;
-    if (mm > 0.0 && isfinite(mm)) frexp(mm, &e);
-    s_E = (mm > 0.0 && isfinite(mm)) ? e - 7 : 0;
+    s_E = slice_exponent(mm);
     J.expo[g] = s_E;
   }
   __syncthreads();
   const int E = s_E;
-  for (int k = threadIdx.x; k < kc; k += blockDim.x) {
-    int dr[kMaxSlices], di[kMaxSlices];
-    bool bad = false;
-    if (k < J.K) {
-      double2 v = col[k];
+  for (int j = threadIdx.x; j < kc; j += blockDim.x) {
+    const int blk = j / hp, l = j - blk * hp;
+    const bool zero = (l >= P.N_L);
+    double2 v = make_double2(0.0, 0.0);
+    if (!zero) {
+      const int k = blk * P.N_L + l;
+      v = col[k];
       if (J.u) {
         v.x *= J.u[k];
         v.y *= J.u[k];
       }
-      bad = !(isfinite(v.x) && isfinite(v.y));
-      digits_of(v.x, E, s, dr);
-      digits_of(v.y, E, s, di);
-    } else {
-#pragma unroll
-      for (int p = 0; p < kMaxSlices; ++p) dr[p] = di[p] = 0;
     }
-#pragma unroll
-    for (int p = 0; p < kMaxSlices; ++p) {
-      if (p < s) {
-        const float sc = __int_as_float((127 - 9 * p) << 23);  // 2^{-9p}
-        uint32_t pl, rt;
-        if (bad) {
-          pl = rt = 0x7FC07FC0u;  // NaN pair: propagates through the MMA
-        } else {
-          pl = (uint32_t)bf16_bits((float)dr[p] * sc) |
-               ((uint32_t)bf16_bits((float)di[p] * sc) << 16);
-          rt = (uint32_t)bf16_bits((float)di[p] * sc) |
-               ((uint32_t)bf16_bits((float)(-dr[p]) * sc) << 16);
-        }
-        ((uint32_t*)(J.plain + p * slice_elems + (size_t)g * J.kpad))[k] = pl;
-        if (J.rot) ((uint32_t*)(J.rot + p * slice_elems + (size_t)g * J.kpad))[k] = rt;
-      }
+    put_slices(v, zero, E, s, J.plain, J.rot, slice_elems, (size_t)g * kpad + 2 * (size_t)j);
+  }
+}
+
+// Slices of the per-atom operators (k-independent, once per factorisation):
+// job 0: MZ[a] (N_L x 2N_L), K = [A part | B part] = 2P; job 1: M2[a] (N_L x N_L),
+// K = P.  Real row n = 2L + c of output row L: c = 0 gives Re, c = 1 gives Im:
+//   row 2L:   (Re M(L,k), -Im M(L,k)) pairs;   row 2L+1: (Im M(L,k), Re M(L,k)).
+// Layout [a][p][n_pad][Kop]; one exponent per (a, n), shared by rows 2L, 2L+1.
+__global__ void __launch_bounds__(128) k_slice_op(const double2* __restrict__ M, int job, int N_A,
+                                                  int N_L, int P, int n_pad, int s,
+                                                  uint16_t* __restrict__ out,
+                                                  int* __restrict__ expo) {
+  const int a = blockIdx.y, n = blockIdx.x;  // n < n_pad
+  const int parts = job == 0 ? 2 : 1;
+  const int Kop = parts * P;
+  const size_t slice_elems = (size_t)n_pad * Kop;
+  uint16_t* base = out + (size_t)a * s * slice_elems;
+  const int L = n >> 1, c = n & 1;
+  const int ldM = N_L;
+  const double2* Ma = M + (size_t)a * N_L * (parts * N_L);
+  __shared__ double red[4];
+  __shared__ int s_E;
+  double m = 0.0;
+  if (L < N_L)
+    for (int k = threadIdx.x; k < parts * N_L; k += blockDim.x) {
+      const double2 v = Ma[L + (size_t)k * ldM];
+      m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
     }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double mm = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
+    s_E = slice_exponent(mm);
+    expo[(size_t)a * n_pad + n] = s_E;
+  }
+  __syncthreads();
+  const int E = s_E;
+  const int hp = P / 2;
+  for (int j = threadIdx.x; j < Kop / 2; j += blockDim.x) {
+    const int part = j / hp, l = j - part * hp;
+    const bool zero = (L >= N_L) || (l >= N_L);
+    double2 v = make_double2(0.0, 0.0);
+    if (!zero) {
+      const double2 mv = Ma[L + (size_t)(part * N_L + l) * ldM];
+      v = c == 0 ? make_double2(mv.x, -mv.y) : make_double2(mv.y, mv.x);
+    }
+    put_slices(v, zero, E, s, base, nullptr, slice_elems, (size_t)n * Kop + 2 * (size_t)j);
   }
 }
 
@@ -575,31 +775,30 @@ bool encode_map(CUtensorMap* m, const uint16_t* base, int kpad, int rows_total) 
 
 }  // namespace
 
-static inline int kpad_of(int K) { return ((2 * K + KB - 1) / KB) * KB; }
 static inline int rows_pad_of(int N_G) { return ((N_G + ROWS_ALIGN - 1) / ROWS_ALIGN) * ROWS_ALIGN; }
+// Padded real length of one block of N_L complex rows (multiple of KB: 32 bytes).
+static inline int block_pad(int N_L) { return ((2 * N_L + KB - 1) / KB) * KB; }
+// Operator rows (2 N_L real rows) padded to whole 128-row MMA tiles.
+static inline int op_rows_pad(int N_L) { return ((2 * N_L + BN - 1) / BN) * BN; }
 
-// Complex rows (K) of each source and whether it needs the rotated copy.
-static void source_shape(int src, int K, int N_L, int n_fail, int& rows, bool& rot) {
+// Blocks (of N_L complex rows) of each source and whether it needs the rotated copy.
+static void source_shape(int src, int N_A, int n_fail, int& nblk, bool& rot) {
   rot = (src != SRC_AF);
-  rows = (src == SRC_AF || src == SRC_X) ? n_fail * N_L : K;
-}
-
-static size_t slicebuf_bytes(int s, int rows_pad, int Kc, bool rot) {
-  const size_t one = (size_t)s * rows_pad * kpad_of(Kc) * 2;
-  return (rot ? 2 : 1) * one + sizeof(int) * rows_pad;
+  nblk = (src == SRC_AF || src == SRC_X) ? n_fail : N_A;
 }
 
 size_t hs_plan_s::split_ws_bytes(int N_G, int n_fail) const {
   if (precision != HS_SPLIT_BF16) return 0;
-  const int K = N_A * N_L;
   const int nf = n_fail > 0 ? n_fail : 1;
   const int rp = rows_pad_of(N_G);
+  const size_t P = (size_t)block_pad(N_L);
   size_t b = 0;
   for (int src = 0; src < NSRC; ++src) {
-    int rows;
+    int nblk;
     bool rot;
-    source_shape(src, K, N_L, nf, rows, rot);
-    b += slicebuf_bytes(slices, rp, rows, rot);
+    source_shape(src, N_A, nf, nblk, rot);
+    const size_t one = (size_t)slices * rp * nblk * P * 2;
+    b += (rot ? 2 : 1) * one + sizeof(int) * rp;
   }
   return b;
 }
@@ -607,17 +806,17 @@ size_t hs_plan_s::split_ws_bytes(int N_G, int n_fail) const {
 int hs_plan_s::split_ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st, bool async) {
   if (precision != HS_SPLIT_BF16) return HS_OK;
   if (!get_encode()) return HS_ECUDA;
-  const int K = N_A * N_L;
   const int rp = rows_pad_of(N_G);
+  const size_t P = (size_t)block_pad(N_L);
   auto al = [&](void** ptr, size_t bytes) -> bool {
     return (async ? hs_malloc_async(ptr, bytes, st, hs_serve_pool(this)) : cudaMalloc(ptr, bytes)) ==
            cudaSuccess;
   };
   for (int src = 0; src < NSRC; ++src) {
-    int rows;
+    int nblk;
     bool rot;
-    source_shape(src, K, N_L, n_fail, rows, rot);
-    const size_t one = (size_t)slices * rp * kpad_of(rows) * 2;
+    source_shape(src, N_A, n_fail, nblk, rot);
+    const size_t one = (size_t)slices * rp * nblk * P * 2;
     if (!al((void**)&w.sb[src].plain, one)) return HS_ENOMEM;
     if (rot && !al((void**)&w.sb[src].rot, one)) return HS_ENOMEM;
     if (!al((void**)&w.sb[src].expo, sizeof(int) * rp)) return HS_ENOMEM;
@@ -625,125 +824,219 @@ int hs_plan_s::split_ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st
   return HS_OK;
 }
 
-int hs_plan_s::split_enqueue(const SegList& sS, const SegList& sH, int N_G, double2* H,
-                             double2* S, Workspace& w, cudaStream_t st, bool timed) {
+size_t hs_plan_s::split_fixed_bytes() const {
+  if (precision != HS_SPLIT_BF16) return 0;
+  const size_t P = (size_t)block_pad(N_L), np = (size_t)op_rows_pad(N_L);
+  return (size_t)N_A * slices * np * (3 * P) * 2 + 2 * sizeof(int) * N_A * np;
+}
+
+int hs_plan_s::split_plan_alloc() {
+  if (precision != HS_SPLIT_BF16) return HS_OK;
+  if (!get_encode()) return HS_ECUDA;
+  const size_t P = (size_t)block_pad(N_L), np = (size_t)op_rows_pad(N_L);
+  const size_t zb = (size_t)N_A * slices * np * 2 * P * 2, wb = zb / 2;
+  if (cudaMalloc((void**)&op_slices[0], zb) != cudaSuccess ||
+      cudaMalloc((void**)&op_slices[1], wb) != cudaSuccess ||
+      cudaMalloc((void**)&op_expo[0], sizeof(int) * N_A * np) != cudaSuccess ||
+      cudaMalloc((void**)&op_expo[1], sizeof(int) * N_A * np) != cudaSuccess) {
+    cudaGetLastError();
+    return HS_ENOMEM;
+  }
+  return HS_OK;
+}
+
+void hs_plan_s::split_plan_release() {
+  for (int j = 0; j < 2; ++j) {
+    if (op_slices[j]) cudaFree(op_slices[j]);
+    if (op_expo[j]) cudaFree(op_expo[j]);
+    op_slices[j] = nullptr;
+    op_expo[j] = nullptr;
+  }
+}
+
+// Slice MZ and M2 (k-independent) after every factorisation.
+int hs_plan_s::split_factor(cudaStream_t st) {
+  if (precision != HS_SPLIT_BF16) return HS_OK;
+  const int P = block_pad(N_L), np = op_rows_pad(N_L);
+  k_slice_op<<<dim3(np, N_A), 128, 0, st>>>(MZ, 0, N_A, N_L, P, np, slices, op_slices[0],
+                                             op_expo[0]);
+  HS_CUDA_TRY(cudaGetLastError());
+  k_slice_op<<<dim3(np, N_A), 128, 0, st>>>(M2, 1, N_A, N_L, P, np, slices, op_slices[1],
+                                             op_expo[1]);
+  HS_CUDA_TRY(cudaGetLastError());
+  return HS_OK;
+}
+
+static int set_smem(const void* fn, size_t smem) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                 cudaSuccess
+             ? HS_OK
+             : HS_ECUDA;
+}
+
+int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const double* U,
+                             int N_G, double2* H, double2* S, Workspace& w, cudaStream_t st,
+                             bool timed) {
   const int K = N_A * N_L;
   const int N_h = N_A - N_f;
   const int s = slices;
   const int rp = rows_pad_of(N_G);
+  const int Pp = block_pad(N_L);
+  const int np = op_rows_pad(N_L);
   if (rows_pad_of(w.N_G) < rp || w.n_fail < N_f || !w.sb[SRC_A].plain) return HS_EINVAL;
-  // sources: sS.s[0] = (A, A), sS.s[1] = (B, B, U), sH.s[0] = (Z, B), then (Y, Y), (A_f, X_f)
-  const Seg& sA = sS.s[0];
-  const Seg& sUB = sS.s[1];
-  const Seg& sZ = sH.s[0];
-  const double2* Yp = nullptr;
-  const double2* AFp = nullptr;
-  const double2* Xp = nullptr;
-  int ldW = K, ldAF = 1;
-  for (int i = 2; i < sH.n; ++i) {
-    if (sH.s[i].L == sH.s[i].R) {
-      Yp = sH.s[i].L;
-      ldW = sH.s[i].ldL;
-    } else {
-      AFp = sH.s[i].L;
-      ldAF = sH.s[i].ldL;
-      Xp = sH.s[i].R;
-    }
-  }
-  SliceParams sp{};
-  sp.s = s;
-  sp.N_G = N_G;
-  sp.rows_pad = rp;
-  int nj = 0;
-  auto job = [&](int src, const double2* X, int ldX, int Kr, const double* u) {
-    SliceBuf& b = w.sb[src];
-    sp.job[nj++] = SliceJob{X, u, b.plain, b.rot, b.expo, ldX, Kr, kpad_of(Kr)};
+
+  // pipeline geometry shared by both kernel modes
+  const int stage_bytes = 4 * s * TILE_BYTES;
+  const int budget = 227 * 1024 - 1024 - 256;
+  int n_stage = budget / stage_bytes;
+  if (n_stage > 8) n_stage = 8;
+  if (n_stage < 2) return HS_EINVAL;
+  const size_t smem = (size_t)n_stage * stage_bytes + 1024 + 256;
+
+  auto slice_launch = [&](SliceParams& sp, int nj) -> int {
+    sp.s = s;
+    sp.N_G = N_G;
+    sp.rows_pad = rp;
+    sp.N_L = N_L;
+    sp.P = Pp;
+    k_slice<<<dim3(rp, nj), 256, 0, st>>>(sp);
+    HS_CUDA_TRY(cudaGetLastError());
+    return HS_OK;
   };
-  job(SRC_A, sA.L, sA.ldL, K, nullptr);
-  job(SRC_UB, sUB.L, sUB.ldL, K, sUB.u);
-  job(SRC_Z, sZ.L, sZ.ldL, K, nullptr);
-  job(SRC_B, sZ.R, sZ.ldR, K, nullptr);
-  if (N_h > 0) job(SRC_Y, Yp, ldW, N_h * N_L, nullptr);
-  if (N_f > 0) {
-    job(SRC_AF, AFp, ldAF, N_f * N_L, nullptr);
-    job(SRC_X, Xp, ldW, N_f * N_L, nullptr);
+  auto job = [&](SliceParams& sp, int& nj, int src, const double2* X, int ldX, int nblk,
+                 const double* u) {
+    SliceBuf& b = w.sb[src];
+    sp.job[nj++] = SliceJob{X, u, b.plain, b.rot, b.expo, ldX, nblk};
+  };
+
+  // 1. slice the inputs A, U.B, B
+  {
+    SliceParams sp{};
+    int nj = 0;
+    job(sp, nj, SRC_A, A, ldAB, N_A, nullptr);
+    job(sp, nj, SRC_UB, B, ldAB, N_A, U);
+    job(sp, nj, SRC_B, B, ldAB, N_A, nullptr);
+    int rc = slice_launch(sp, nj);
+    if (rc) return rc;
   }
-  k_slice<<<dim3(rp, nj), 256, 0, st>>>(sp);
-  HS_CUDA_TRY(cudaGetLastError());
+  if (timed) HS_CUDA_TRY(cudaEventRecord(ev[9], st));
+
+  // 2. per-atom products on the tensor cores: Z and W2 = [Y; X] in FP64
+  {
+    SplitParams PA;
+    std::memset(&PA, 0, sizeof(PA));
+    if (!encode_map(&PA.maps[0], w.sb[SRC_A].plain, N_A * Pp, s * rp) ||
+        !encode_map(&PA.maps[1], w.sb[SRC_B].plain, N_A * Pp, s * rp) ||
+        !encode_map(&PA.maps[2], op_slices[0], 2 * Pp, N_A * s * np) ||
+        !encode_map(&PA.maps[3], op_slices[1], Pp, N_A * s * np))
+      return HS_ECUDA;
+    AtomsArgs& at = PA.at;
+    at.mA = 0;
+    at.mB = 1;
+    at.mOp[0] = 2;
+    at.mOp[1] = 3;
+    at.eA = w.sb[SRC_A].expo;
+    at.eB = w.sb[SRC_B].expo;
+    at.eOp[0] = op_expo[0];
+    at.eOp[1] = op_expo[1];
+    at.slot = slot_d;
+    at.Z = w.Z;
+    at.W2 = w.W2;
+    at.ld = K;
+    at.N_A = N_A;
+    at.N_L = N_L;
+    at.P = Pp;
+    at.n_pad = np;
+    at.ntile = np / BN;
+    at.ngblk = rp / BM;
+    PA.s = s;
+    PA.n_stage = n_stage;
+    PA.N_G = N_G;
+    PA.rows_pad = rp;
+    PA.err = err_d;
+    int rc = set_smem((const void*)k_split_gemm<MODE_ATOMS>, smem);
+    if (rc) return rc;
+    const int grid = at.ngblk * at.ntile * 2 * N_A;
+    k_split_gemm<MODE_ATOMS><<<grid, NUM_THREADS, smem, st>>>(PA);
+    HS_CUDA_TRY(cudaGetLastError());
+  }
+  HS_CUDA_TRY(hs_launch_gather_af(A, ldAB, fail_list_d, N_f, N_L, N_G, w.AF, st));
+  if (timed) HS_CUDA_TRY(cudaEventRecord(ev[4], st));
+
+  // 3. slice the per-atom outputs Z, Y, A_f, X
+  {
+    SliceParams sp{};
+    int nj = 0;
+    job(sp, nj, SRC_Z, w.Z, K, N_A, nullptr);
+    if (N_h > 0) job(sp, nj, SRC_Y, w.W2, K, N_h, nullptr);
+    if (N_f > 0) {
+      job(sp, nj, SRC_AF, w.AF, N_f * N_L, N_f, nullptr);
+      job(sp, nj, SRC_X, w.W2 + (size_t)N_h * N_L, K, N_f, nullptr);
+    }
+    int rc = slice_launch(sp, nj);
+    if (rc) return rc;
+  }
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[5], st));
 
-  // tensor maps: index = 2*src + {0 plain, 1 rot} except A_f (plain only)
+  // 4. the two stacked contractions
   SplitParams P;
   std::memset(&P, 0, sizeof(P));
   int map_of[NSRC][2];
   int nm = 0;
-  // a slice array's rows: rp per slice (this call's padding, within capacity)
-  auto add_map = [&](int src, int Kr) -> int {
+  auto add_map = [&](int src, int nblk) -> bool {
     SliceBuf& b = w.sb[src];
     map_of[src][0] = nm;
-    if (!encode_map(&P.maps[nm++], b.plain, kpad_of(Kr), s * rp)) return HS_ECUDA;
+    if (!encode_map(&P.maps[nm++], b.plain, nblk * Pp, s * rp)) return false;
     if (b.rot) {
       map_of[src][1] = nm;
-      if (!encode_map(&P.maps[nm++], b.rot, kpad_of(Kr), s * rp)) return HS_ECUDA;
+      if (!encode_map(&P.maps[nm++], b.rot, nblk * Pp, s * rp)) return false;
     }
-    return HS_OK;
+    return true;
   };
-  int rc = HS_OK;
-  rc |= add_map(SRC_A, K);
-  rc |= add_map(SRC_UB, K);
-  rc |= add_map(SRC_Z, K);
-  rc |= add_map(SRC_B, K);
-  if (N_h > 0) rc |= add_map(SRC_Y, N_h * N_L);
-  if (N_f > 0) {
-    rc |= add_map(SRC_AF, N_f * N_L);
-    rc |= add_map(SRC_X, N_f * N_L);
-  }
-  if (rc != HS_OK) return HS_ECUDA;
-
+  bool ok = add_map(SRC_A, N_A) && add_map(SRC_UB, N_A) && add_map(SRC_Z, N_A) &&
+            add_map(SRC_B, N_A);
+  if (N_h > 0) ok = ok && add_map(SRC_Y, N_h);
+  if (N_f > 0) ok = ok && add_map(SRC_AF, N_f) && add_map(SRC_X, N_f);
+  if (!ok) return HS_ECUDA;
   P.s = s;
+  P.n_stage = n_stage;
   P.N_G = N_G;
   P.ldC = N_G;
   P.nbj = (N_G + BNC - 1) / BNC;
   P.rows_pad = rp;
   P.err = err_d;
-  const int stage_bytes = 4 * s * TILE_BYTES;
-  const int budget = 227 * 1024 - 1024 - 256;
-  P.n_stage = budget / stage_bytes;
-  if (P.n_stage > 8) P.n_stage = 8;
-  if (P.n_stage < 2) return HS_EINVAL;
-  const size_t smem = (size_t)P.n_stage * stage_bytes + 1024 + 256;
-  HS_CUDA_TRY(cudaFuncSetAttribute(k_contract_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
+  int rc = set_smem((const void*)k_split_gemm<MODE_CONTRACT>, smem);
+  if (rc) return rc;
   const int nbi = (N_G + BM - 1) / BM;
   int tiles = 0;
   for (int b = 0; b < nbi; ++b) tiles += std::min(2 * b + 2, P.nbj);
-  auto seg = [&](int srcL, int srcR, int Kr) {
+  auto seg = [&](int srcL, int srcR, int nblk) {
     SplitSeg g;
     g.mL = map_of[srcL][0];
     g.mR = map_of[srcR][0];
     g.mRr = map_of[srcR][1];
-    g.kblocks = kpad_of(Kr) / KB;
+    g.kblocks = nblk * Pp / KB;
     g.eL = w.sb[srcL].expo;
     g.eR = w.sb[srcR].expo;
     return g;
   };
   // S = A^H A + (UB)^H (UB)
   P.nseg = 2;
-  P.seg[0] = seg(SRC_A, SRC_A, K);
-  P.seg[1] = seg(SRC_UB, SRC_UB, K);
+  P.seg[0] = seg(SRC_A, SRC_A, N_A);
+  P.seg[1] = seg(SRC_UB, SRC_UB, N_A);
   P.C = S;
-  k_contract_split<<<tiles, NUM_THREADS, smem, st>>>(P);
+  k_split_gemm<MODE_CONTRACT><<<tiles, NUM_THREADS, smem, st>>>(P);
   HS_CUDA_TRY(cudaGetLastError());
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[6], st));
   // H = Z^H B + B^H Z + Y^H Y + A_f^H X_f
   int n = 0;
-  P.seg[n++] = seg(SRC_Z, SRC_B, K);
-  P.seg[n++] = seg(SRC_B, SRC_Z, K);
-  if (N_h > 0) P.seg[n++] = seg(SRC_Y, SRC_Y, N_h * N_L);
-  if (N_f > 0) P.seg[n++] = seg(SRC_AF, SRC_X, N_f * N_L);
+  P.seg[n++] = seg(SRC_Z, SRC_B, N_A);
+  P.seg[n++] = seg(SRC_B, SRC_Z, N_A);
+  if (N_h > 0) P.seg[n++] = seg(SRC_Y, SRC_Y, N_h);
+  if (N_f > 0) P.seg[n++] = seg(SRC_AF, SRC_X, N_f);
   P.nseg = n;
   P.C = H;
-  k_contract_split<<<tiles, NUM_THREADS, smem, st>>>(P);
+  k_split_gemm<MODE_CONTRACT><<<tiles, NUM_THREADS, smem, st>>>(P);
   HS_CUDA_TRY(cudaGetLastError());
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[7], st));
   return HS_OK;

@@ -72,6 +72,11 @@ struct hs_plan_s {
   double last_factor_ms = 0.0;
   bool factor_pending_info = false;  // hs_set_t ran since the last hs_assemble
 
+  // split form: BF16 slices of MZ (job 0) and M2 (job 1), [a][p][n_pad][Kop], and
+  // one exponent per (atom, operator row); refreshed with every factorisation
+  uint16_t* op_slices[2] = {nullptr, nullptr};
+  int* op_expo[2] = {nullptr, nullptr};
+
   int* err_d = nullptr;  // device error word (bounded waits)
   cudaEvent_t ev[10] = {};
   void* stage[6] = {};   // host-call staging: A, B, T, U, H, S
@@ -85,12 +90,16 @@ struct hs_plan_s {
   int split_ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st, bool async);
   void ws_free(Workspace& w, cudaStream_t st);
   size_t fixed_bytes() const;
+  size_t split_fixed_bytes() const;
+  int split_plan_alloc();
+  void split_plan_release();
+  int split_factor(cudaStream_t st);
   void release();
   int factor(const double2* T_AA, const double2* T_AB, const double2* T_BB);
   int enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G, double2* H,
               double2* S, Workspace& w, cudaStream_t st, bool timed);
-  int split_enqueue(const SegList& sS, const SegList& sH, int N_G, double2* H, double2* S,
-                    Workspace& w, cudaStream_t st, bool timed);
+  int split_enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G,
+                    double2* H, double2* S, Workspace& w, cudaStream_t st, bool timed);
   int check_device_error();
   void fill_info(hs_info* info, bool factored);
   bool serve_busy();
