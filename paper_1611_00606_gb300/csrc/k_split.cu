@@ -46,8 +46,12 @@ constexpr int ROWS_ALIGN = 128;
 constexpr int kMaxMaps = 13;
 constexpr int kMaxJobs = 7;
 constexpr int TILE_BYTES = 64 * KB * 2;  // one 64-row TMA box: 2 KB
-constexpr int NUM_THREADS = 320;         // warp 0 TMA, warp 1 MMA, warps 2..9 drain
+constexpr int NUM_DRAIN_WARPS = 16;     // four per TMEM lane quarter
+constexpr int NUM_THREADS = 64 + 32 * NUM_DRAIN_WARPS;  // warp 0 TMA, warp 1 MMA, then drain
 constexpr uint64_t kWaitNs = 2000000000ull;  // bounded waits: 2 s
+// epilogue staging in the (then idle) stage area: (hi, lo) float2 for 128 rows x
+// 2 strips x 64 columns, plus 128 row and 128 column exponents
+constexpr int STAGING_BYTES = 2 * 64 * 128 * 8 + 256 * 4;
 
 // ------------------------------------------------------------------ PTX helpers
 
@@ -168,13 +172,13 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 }
 
 
-// Drain one 32-column strip of the four window accumulators (level k at
-// column offset k*BN) into (hi, lo) pairs.  rsc = 2^eL (this thread's row);
-// lane c of csc holds 2^eR of column c.
-__device__ __forceinline__ void drain_cols(uint32_t taddr, int s, float rsc, float csc,
-                                           float (&hi)[32], float (&lo)[32]) {
+// Drain 16 TMEM columns of the four window accumulators (level k at column
+// offset k*BN) into (hi, lo) pairs kept in units of the current segment's
+// scale 2^(E_row + E_col): the window sums are exact integers (levels 0-2), so
+// levels 0, 1, 2 go through an error-free TwoSum into hi and levels >= 3 into lo.
+__device__ __forceinline__ void drain16(uint32_t taddr, int s, float (&hi)[16], float (&lo)[16]) {
 #pragma unroll
-  for (int c0 = 0; c0 < 32; c0 += 4) {
+  for (int c0 = 0; c0 < 16; c0 += 4) {
     float v0[4], v1[4], v2[4], v3[4];
     tmem_ld4(taddr + c0, v0);
     tmem_ld4(taddr + BN + c0, v1);
@@ -183,13 +187,17 @@ __device__ __forceinline__ void drain_cols(uint32_t taddr, int s, float rsc, flo
     tmem_wait_ld();
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const float sc = rsc * __shfl_sync(0xffffffffu, csc, c0 + c);
-      two_sum_acc(hi[c0 + c], lo[c0 + c], v0[c] * sc);
-      two_sum_acc(hi[c0 + c], lo[c0 + c], v1[c] * sc);
-      if (s >= 3) two_sum_acc(hi[c0 + c], lo[c0 + c], v2[c] * sc);
-      if (s >= 4) lo[c0 + c] = fmaf(v3[c], sc, lo[c0 + c]);
+      two_sum_acc(hi[c0 + c], lo[c0 + c], v0[c]);
+      two_sum_acc(hi[c0 + c], lo[c0 + c], v1[c]);
+      if (s >= 3) two_sum_acc(hi[c0 + c], lo[c0 + c], v2[c]);
+      if (s >= 4) lo[c0 + c] += v3[c];
     }
   }
+}
+
+// Exact FP64 power of two (|e| well inside the normal range).
+__device__ __forceinline__ double pow2d(int e) {
+  return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
 // ------------------------------------------------------------------ slice-GEMM kernel
@@ -338,7 +346,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   const int NS = P.n_stage;
   const uint32_t a_bytes = (uint32_t)s * 2 * TILE_BYTES;   // s slices x 128 rows
   const uint32_t stage_bytes = 2 * a_bytes;                 // A part + B part
-  uint64_t* full = (uint64_t*)(smem + NS * stage_bytes);
+  const uint32_t ring_bytes = max(NS * stage_bytes, (uint32_t)STAGING_BYTES);
+  uint64_t* full = (uint64_t*)(smem + ring_bytes);
   uint64_t* empty = full + NS;
   uint64_t* acc_full = empty + NS;
   uint64_t* acc_empty = acc_full + 1;
@@ -354,7 +363,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
       mbar_init(&empty[i], 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 8);
+    mbar_init(acc_empty, NUM_DRAIN_WARPS);
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -481,29 +490,44 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
         if (globaltimer() - t0 > kWaitNs) break;
     }
   } else {
-    // ---------------- drain warps 2..9: TMEM -> double-float accumulators
-    const int q4 = warp & 3;        // TMEM lane quarter this warp may access
-    const int h = (warp - 2) >> 2;  // 32-column half of each 64-column strip
+    // ---------------- drain warps: TMEM -> double-float accumulators
+    const int q4 = warp & 3;         // TMEM lane quarter this warp may access
+    const int cg = (warp - 2) >> 2;  // 16-column group of each 64-column strip
     const int row = T.i0 + 32 * q4 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16);
-    float h0[32], l0[32], h1[32], l1[32];  // strip 0 (TMEM cols < 64), strip 1
+    const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(16 * cg);
+    float h0[16], l0[16], h1[16], l1[16];  // strip 0 (TMEM cols < 64), strip 1
 #pragma unroll
-    for (int c = 0; c < 32; ++c) h0[c] = l0[c] = h1[c] = l1[c] = 0.f;
+    for (int c = 0; c < 16; ++c) h0[c] = l0[c] = h1[c] = l1[c] = 0.f;
     int nwin = 0;
     bool ok = true;
+    int eRow = 0, eC0 = 0, eC1 = 0;  // current segment's exponents (lane c: column c)
     for (int sg = 0; sg < T.nseg && ok; ++sg) {
       const SegInfo si = seg_info<MODE>(P, T, sg);
-      const float rsc = pow2f(si.eRow[row]);
-      const float csc0 = pow2f(si.eC0[32 * h + lane]);  // lane c: column c's scale
-      const float csc1 = pow2f(si.eC1[32 * h + lane]);
+      const int nRow = si.eRow[row];
+      const int nC0 = si.eC0[16 * cg + (lane & 15)];
+      const int nC1 = si.eC1[16 * cg + (lane & 15)];
+      if (sg > 0) {  // move the pairs into the new segment's units (exact powers of two)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float f0 = pow2f(eRow - nRow + __shfl_sync(0xffffffffu, eC0 - nC0, c));
+          const float f1 = pow2f(eRow - nRow + __shfl_sync(0xffffffffu, eC1 - nC1, c));
+          h0[c] *= f0;
+          l0[c] *= f0;
+          h1[c] *= f1;
+          l1[c] *= f1;
+        }
+      }
+      eRow = nRow;
+      eC0 = nC0;
+      eC1 = nC1;
       for (int w0 = 0; w0 < si.kblocks; w0 += WIN) {
         if (!mbar_wait(acc_full, (uint32_t)nwin & 1u, abort_flag)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        drain_cols(tl + (uint32_t)(32 * h), s, rsc, csc0, h0, l0);
-        drain_cols(tl + (uint32_t)(BNC + 32 * h), s, rsc, csc1, h1, l1);
+        drain16(tl, s, h0, l0);
+        drain16(tl + (uint32_t)BNC, s, h1, l1);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acc_empty);
@@ -513,31 +537,56 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
     if (!ok) {
       atomicExch(P.err, 3);
       *abort_flag = 1;
-    } else if (MODE == MODE_CONTRACT) {
-      if (row < P.N_G) {
+    }
+    // Epilogue through shared memory (the pipeline stages are idle now: every
+    // stage was consumed by an MMA that completed before the last acc_full):
+    // stage (hi, lo) pairs and the last segment's exponents, then write the
+    // tile out with consecutive threads on consecutive output addresses.
+    float2* stg = (float2*)smem;                       // [2 strips][64 cols][128 rows]
+    int* s_erow = (int*)(smem + 2 * 64 * 128 * sizeof(float2));
+    int* s_ecol = s_erow + 128;                        // [2][64]
+    const int r = 32 * q4 + lane;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const int j = T.j0 + 32 * h + c;
-          if (j < P.N_G)
-            P.C[row + (size_t)j * P.ldC] =
-                make_double2((double)h0[c] + (double)l0[c], (double)h1[c] + (double)l1[c]);
+    for (int c = 0; c < 16; ++c) {
+      stg[(0 * 64 + 16 * cg + c) * 128 + r] = make_float2(h0[c], l0[c]);
+      stg[(1 * 64 + 16 * cg + c) * 128 + r] = make_float2(h1[c], l1[c]);
+    }
+    if (cg == 0) s_erow[r] = eRow;
+    if (q4 == 0 && lane < 16) {
+      s_ecol[16 * cg + lane] = eC0;
+      s_ecol[64 + 16 * cg + lane] = eC1;
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * NUM_DRAIN_WARPS) : "memory");
+    const int dt = threadIdx.x - 64;  // 0 .. 32*NUM_DRAIN_WARPS-1
+    if (ok && !*abort_flag) {
+      if (MODE == MODE_CONTRACT) {
+        for (int idx = dt; idx < 64 * 128; idx += 32 * NUM_DRAIN_WARPS) {
+          const int jj = idx >> 7, ii = idx & 127;
+          const int i = T.i0 + ii, j = T.j0 + jj;
+          if (i < P.N_G && j < P.N_G) {
+            const double sc = pow2d(s_erow[ii] + s_ecol[jj]);
+            const float2 re = stg[jj * 128 + ii], im = stg[(64 + jj) * 128 + ii];
+            P.C[i + (size_t)j * P.ldC] = make_double2(((double)re.x + (double)re.y) * sc,
+                                                      ((double)im.x + (double)im.y) * sc);
+          }
         }
-      }
-    } else if (row < P.N_G) {
-      const AtomsArgs& A = P.at;
-      double2* out = (T.job == 0 ? A.Z + (size_t)T.a * A.N_L
-                                 : A.W2 + (size_t)A.slot[T.a] * A.N_L) + (size_t)row * A.ld;
-      const int L0 = (T.n0 >> 1) + 16 * h;  // first output row of strip 0 for this warp
-#pragma unroll
-      for (int c = 0; c < 32; c += 2) {
-        const int L = L0 + (c >> 1);
-        if (L < A.N_L)
-          out[L] = make_double2((double)h0[c] + (double)l0[c],
-                                (double)h0[c + 1] + (double)l0[c + 1]);
-        const int L1 = L + 32;
-        if (L1 < A.N_L)
-          out[L1] = make_double2((double)h1[c] + (double)l1[c],
-                                 (double)h1[c + 1] + (double)l1[c + 1]);
+      } else {
+        const AtomsArgs& A = P.at;
+        double2* out = T.job == 0 ? A.Z + (size_t)T.a * A.N_L
+                                  : A.W2 + (size_t)A.slot[T.a] * A.N_L;
+        const int Lb = T.n0 >> 1;
+        for (int idx = dt; idx < 64 * 128; idx += 32 * NUM_DRAIN_WARPS) {
+          const int gg = idx >> 6, ll = idx & 63;  // tile row, local output row
+          const int g = T.i0 + gg, L = Lb + ll;
+          if (g < P.N_G && L < A.N_L) {
+            const int nl = 2 * ll, st = nl >> 6, c = nl & 63;
+            const float2 re = stg[(st * 64 + c) * 128 + gg], im = stg[(st * 64 + c + 1) * 128 + gg];
+            const double sre = pow2d(s_erow[gg] + s_ecol[st * 64 + c]);
+            const double sim = pow2d(s_erow[gg] + s_ecol[st * 64 + c + 1]);
+            out[(size_t)L + (size_t)g * A.ld] = make_double2(((double)re.x + (double)re.y) * sre,
+                                                             ((double)im.x + (double)im.y) * sim);
+          }
+        }
       }
     }
   }
@@ -891,7 +940,7 @@ int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const
   int n_stage = budget / stage_bytes;
   if (n_stage > 8) n_stage = 8;
   if (n_stage < 2) return HS_EINVAL;
-  const size_t smem = (size_t)n_stage * stage_bytes + 1024 + 256;
+  const size_t smem = std::max((size_t)n_stage * stage_bytes, (size_t)STAGING_BYTES) + 1024 + 256;
 
   auto slice_launch = [&](SliceParams& sp, int nj) -> int {
     sp.s = s;
