@@ -100,12 +100,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
     }
   }
 }
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
+// One 64-row x 16-element box of a blocked slice array (coordinates: k block,
+// 64-row block, plane = slice [+ atom]); the box is contiguous in global memory.
+__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* map, int kb, int rb,
+                                              int plane, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(0), "r"(0), "r"(kb), "r"(rb), "r"(plane), "r"(smem_u32(bar))
       : "memory");
 }
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
@@ -251,13 +253,14 @@ struct __align__(64) SplitParams {
   AtomsArgs at;
 };
 
-// Where one K segment of this CTA's tile lives.
+// Where one K segment of this CTA's tile lives (blocked slice arrays:
+// plane = slice p (+ atom * s for operators), 64-row blocks, 16-wide K blocks).
 struct SegInfo {
   const CUtensorMap* mL;
   const CUtensorMap* mR1;
   const CUtensorMap* mR2;
-  int xL, yL, ysL;          // L side: x base, row base (slice 0), rows per slice
-  int xR, yR1, yR2, ysR;    // R side: x base, row bases of the two 64-row boxes, rows per slice
+  int kbL, rbL, plL;        // L side: first K block, first 64-row block, plane of slice 0
+  int kbR, rbR1, rbR2, plR; // R side: first K block, row blocks of the two boxes, plane of slice 0
   int kblocks;
   const int* eRow;          // indexed by the tile's absolute row
   const int* eC0;           // column exponents of TMEM columns [0, 64) (+ column in strip)
@@ -307,13 +310,13 @@ __device__ __forceinline__ SegInfo seg_info(const SplitParams& P, const TileId& 
     si.mL = &P.maps[S.mL];
     si.mR1 = &P.maps[S.mR];
     si.mR2 = &P.maps[S.mRr];
-    si.xL = 0;
-    si.yL = t.i0;
-    si.ysL = P.rows_pad;
-    si.xR = 0;
-    si.yR1 = t.j0;
-    si.yR2 = t.j0;
-    si.ysR = P.rows_pad;
+    si.kbL = 0;
+    si.rbL = t.i0 >> 6;
+    si.plL = 0;
+    si.kbR = 0;
+    si.rbR1 = t.j0 >> 6;
+    si.rbR2 = t.j0 >> 6;
+    si.plR = 0;
     si.kblocks = S.kblocks;
     si.eRow = S.eL;
     si.eC0 = S.eR + t.j0;
@@ -322,13 +325,13 @@ __device__ __forceinline__ SegInfo seg_info(const SplitParams& P, const TileId& 
     const AtomsArgs& A = P.at;
     si.mL = &P.maps[sg == 0 ? A.mA : A.mB];
     si.mR1 = si.mR2 = &P.maps[A.mOp[t.job]];
-    si.xL = t.a * A.P;
-    si.yL = t.i0;
-    si.ysL = P.rows_pad;
-    si.xR = sg * A.P;  // Z operator: A part in [0, P), B part in [P, 2P)
-    si.yR1 = t.a * P.s * A.n_pad + t.n0;
-    si.yR2 = si.yR1 + 64;
-    si.ysR = A.n_pad;
+    si.kbL = t.a * (A.P / KB);
+    si.rbL = t.i0 >> 6;
+    si.plL = 0;
+    si.kbR = sg * (A.P / KB);  // Z operator: A part in [0, P), B part in [P, 2P)
+    si.rbR1 = t.n0 >> 6;
+    si.rbR2 = (t.n0 >> 6) + 1;
+    si.plR = t.a * P.s;
     si.kblocks = A.P / KB;
     si.eRow = sg == 0 ? A.eA : A.eB;
     si.eC0 = A.eOp[t.job] + t.a * A.n_pad + t.n0;
@@ -337,12 +340,34 @@ __device__ __forceinline__ SegInfo seg_info(const SplitParams& P, const TileId& 
   return si;
 }
 
-template <int MODE>
+// Issue one stage's slice-pair MMAs: pairs (p, q) with p + q < S go to the
+// accumulator of level min(p + q, 3).  Fully unrolled for a compile-time slice
+// count; the descriptors of slice p / q are the stage's base descriptors plus a
+// constant (the 14-bit start-address field holds address >> 4 and stays below
+// 2^14 for any smem address).  `first` = first stage of a window: the first
+// pair of every level overwrites its accumulator instead of adding to it.
+template <int S>
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t ad0, uint64_t bd0, bool first) {
+#pragma unroll
+  for (int p = 0; p < S; ++p) {
+#pragma unroll
+    for (int q = 0; q < S - p; ++q) {
+      constexpr int kStep = (2 * TILE_BYTES) >> 4;
+      const int lvl = p + q;
+      const int acc = lvl < 3 ? lvl : 3;
+      const bool lead = (p == 0 && q == acc);  // first pair of its level within a stage
+      tc_mma_bf16(tmem + acc * BN, ad0 + (uint64_t)(p * kStep), bd0 + (uint64_t)(q * kStep), kIdesc,
+                  (lead && first) ? 0u : 1u);
+    }
+  }
+}
+
+template <int MODE, int S>
 __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_constant__ SplitParams P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = P.s;
+  constexpr int s = S;
   const int NS = P.n_stage;
   const uint32_t a_bytes = (uint32_t)s * 2 * TILE_BYTES;   // s slices x 128 rows
   const uint32_t stage_bytes = 2 * a_bytes;                 // A part + B part
@@ -407,14 +432,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           armed_par = (armed_par & ~(1u << slot)) | (phase << slot);
           const uint32_t sa = smem_u32(smem + slot * stage_bytes);
           const uint32_t sb = sa + a_bytes;
-          const int xl = si.xL + kb * KB, xr = si.xR + kb * KB;
+          const int kl = si.kbL + kb, kr = si.kbR + kb;
           for (int p = 0; p < s; ++p) {
-            const int yl = si.yL + p * si.ysL;
-            tma_load_2d(sa + p * 2 * TILE_BYTES, si.mL, xl, yl, &full[slot]);
-            tma_load_2d(sa + p * 2 * TILE_BYTES + TILE_BYTES, si.mL, xl, yl + 64, &full[slot]);
-            tma_load_2d(sb + p * 2 * TILE_BYTES, si.mR1, xr, si.yR1 + p * si.ysR, &full[slot]);
-            tma_load_2d(sb + p * 2 * TILE_BYTES + TILE_BYTES, si.mR2, xr, si.yR2 + p * si.ysR,
-                        &full[slot]);
+            tma_load_tile(sa + p * 2 * TILE_BYTES, si.mL, kl, si.rbL, si.plL + p, &full[slot]);
+            tma_load_tile(sa + p * 2 * TILE_BYTES + TILE_BYTES, si.mL, kl, si.rbL + 1, si.plL + p,
+                          &full[slot]);
+            tma_load_tile(sb + p * 2 * TILE_BYTES, si.mR1, kr, si.rbR1, si.plR + p, &full[slot]);
+            tma_load_tile(sb + p * 2 * TILE_BYTES + TILE_BYTES, si.mR2, kr, si.rbR2, si.plR + p,
+                          &full[slot]);
           }
           if (++slot == NS) {
             slot = 0;
@@ -457,18 +482,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
             }
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + slot * stage_bytes);
-            const uint32_t sb = sa + a_bytes;
-            const bool first = (kb == w0);
-            for (int p = 0; p < s; ++p) {
-              const uint64_t ad = sdesc_sw32(sa + p * 2 * TILE_BYTES);
-              for (int q = 0; p + q < s; ++q) {
-                const int lvl = p + q;
-                const int acc = lvl < 3 ? lvl : 3;
-                const bool init = first && p == 0 && q == acc;  // first pair of this level
-                tc_mma_bf16(tmem + acc * BN, ad, sdesc_sw32(sb + q * 2 * TILE_BYTES), kIdesc,
-                            init ? 0u : 1u);
-              }
-            }
+            issue_stage<S>(tmem, sdesc_sw32(sa), sdesc_sw32(sa + a_bytes), kb == w0);
             tc_commit(&empty[slot]);
             if (++slot == NS) {
               slot = 0;
@@ -601,11 +615,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
 
 // ------------------------------------------------------------------ slicers
 
-// Padded real-K layout shared by every slice array: complex row k of a source
-// with blocks of N_L rows (atoms or slots) sits at real position
-// (k / N_L) * P + 2 (k % N_L) (+1 for the imaginary part), P = roundup(2 N_L, 16);
-// the gaps hold zeros.  Every atom block therefore starts on a 32-byte TMA
-// boundary, which the per-atom products need.
+// Layout shared by every slice array.  Along K: complex row k of a source with
+// blocks of N_L rows (atoms or slots) sits at real position
+// (k / N_L) * P + 2 (k % N_L) (+1 for the imaginary part), P = roundup(2 N_L, 16),
+// the gaps holding zeros, so every atom block starts on a 16-element boundary.
+// In memory each slice plane is blocked as [64-row block][16-wide K block][64 rows]
+// [16 elements]: one 2 KB tile per (row block, K block), contiguous, which is
+// exactly one TMA box (the TMA applies the 32-byte swizzle on the way to smem).
+__device__ __forceinline__ size_t tile_off(int row, int j, int NKB) {
+  // element offset of the complex pair j (real elements 2j, 2j+1) of a row
+  return ((size_t)((row >> 6) * NKB + (j >> 3)) * 64 + (row & 63)) * 16 + 2 * (j & 7);
+}
 struct SliceJob {
   const double2* X;  // source: nblk * N_L complex rows x N_G, column-major, ld ldX
   const double* u;   // optional real row weight (the U norms), may be null
@@ -701,11 +721,12 @@ __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SlicePara
   __shared__ double red[32];
   __shared__ int s_E;
   const int kc = kpad / 2;  // complex positions per padded row
+  const int NKB = kpad / KB;
   if (g >= P.N_G) {
     for (int k = threadIdx.x; k < kc; k += blockDim.x)
       for (int p = 0; p < s; ++p) {
-        ((uint32_t*)(J.plain + p * slice_elems + (size_t)g * kpad))[k] = 0u;
-        if (J.rot) ((uint32_t*)(J.rot + p * slice_elems + (size_t)g * kpad))[k] = 0u;
+        *(uint32_t*)(J.plain + p * slice_elems + tile_off(g, k, NKB)) = 0u;
+        if (J.rot) *(uint32_t*)(J.rot + p * slice_elems + tile_off(g, k, NKB)) = 0u;
       }
     if (threadIdx.x == 0) J.expo[g] = 0;
     return;
@@ -741,7 +762,7 @@ __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SlicePara
         v.y *= J.u[k];
       }
     }
-    put_slices(v, zero, E, s, J.plain, J.rot, slice_elems, (size_t)g * kpad + 2 * (size_t)j);
+    put_slices(v, zero, E, s, J.plain, J.rot, slice_elems, tile_off(g, j, NKB));
   }
 }
 
@@ -789,7 +810,7 @@ __global__ void __launch_bounds__(128) k_slice_op(const double2* __restrict__ M,
       const double2 mv = Ma[L + (size_t)(part * N_L + l) * ldM];
       v = c == 0 ? make_double2(mv.x, -mv.y) : make_double2(mv.y, mv.x);
     }
-    put_slices(v, zero, E, s, base, nullptr, slice_elems, (size_t)n * Kop + 2 * (size_t)j);
+    put_slices(v, zero, E, s, base, nullptr, slice_elems, tile_off(n, j, Kop / KB));
   }
 }
 
@@ -809,14 +830,17 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-bool encode_map(CUtensorMap* m, const uint16_t* base, int kpad, int rows_total) {
+// Tensor map over a blocked slice array: dims (16 elements, 64 rows, NKB K blocks,
+// NRB row blocks, planes), one box = one contiguous 2 KB tile.
+bool encode_tiles(CUtensorMap* m, const uint16_t* base, int NKB, int NRB, int planes) {
   auto fn = get_encode();
   if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows_total};
-  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
-  cuuint32_t box[2] = {(cuuint32_t)KB, 64u};
-  cuuint32_t estr[2] = {1u, 1u};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+  cuuint64_t dims[5] = {(cuuint64_t)KB, 64u, (cuuint64_t)NKB, (cuuint64_t)NRB, (cuuint64_t)planes};
+  cuuint64_t strides[4] = {(cuuint64_t)KB * 2, (cuuint64_t)TILE_BYTES,
+                           (cuuint64_t)NKB * TILE_BYTES, (cuuint64_t)NRB * NKB * TILE_BYTES};
+  cuuint32_t box[5] = {(cuuint32_t)KB, 64u, 1u, 1u, 1u};
+  cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -923,6 +947,33 @@ static int set_smem(const void* fn, size_t smem) {
              : HS_ECUDA;
 }
 
+template <int MODE, int S>
+static int launch_one(int grid, size_t smem, cudaStream_t st, const SplitParams& P) {
+  int rc = set_smem((const void*)k_split_gemm<MODE, S>, smem);
+  if (rc) return rc;
+  k_split_gemm<MODE, S><<<grid, NUM_THREADS, smem, st>>>(P);
+  return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
+}
+
+template <int MODE>
+static int launch_mode(int s, int grid, size_t smem, cudaStream_t st, const SplitParams& P) {
+  switch (s) {
+    case 2: return launch_one<MODE, 2>(grid, smem, st, P);
+    case 3: return launch_one<MODE, 3>(grid, smem, st, P);
+    case 4: return launch_one<MODE, 4>(grid, smem, st, P);
+    case 5: return launch_one<MODE, 5>(grid, smem, st, P);
+    case 6: return launch_one<MODE, 6>(grid, smem, st, P);
+    case 7: return launch_one<MODE, 7>(grid, smem, st, P);
+    default: return HS_EINVAL;
+  }
+}
+
+static int launch_gemm(int mode, int s, int grid, size_t smem, cudaStream_t st,
+                       const SplitParams& P) {
+  return mode == MODE_CONTRACT ? launch_mode<MODE_CONTRACT>(s, grid, smem, st, P)
+                               : launch_mode<MODE_ATOMS>(s, grid, smem, st, P);
+}
+
 int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const double* U,
                              int N_G, double2* H, double2* S, Workspace& w, cudaStream_t st,
                              bool timed) {
@@ -974,10 +1025,10 @@ int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const
   {
     SplitParams PA;
     std::memset(&PA, 0, sizeof(PA));
-    if (!encode_map(&PA.maps[0], w.sb[SRC_A].plain, N_A * Pp, s * rp) ||
-        !encode_map(&PA.maps[1], w.sb[SRC_B].plain, N_A * Pp, s * rp) ||
-        !encode_map(&PA.maps[2], op_slices[0], 2 * Pp, N_A * s * np) ||
-        !encode_map(&PA.maps[3], op_slices[1], Pp, N_A * s * np))
+    if (!encode_tiles(&PA.maps[0], w.sb[SRC_A].plain, N_A * Pp / KB, rp / 64, s) ||
+        !encode_tiles(&PA.maps[1], w.sb[SRC_B].plain, N_A * Pp / KB, rp / 64, s) ||
+        !encode_tiles(&PA.maps[2], op_slices[0], 2 * Pp / KB, np / 64, N_A * s) ||
+        !encode_tiles(&PA.maps[3], op_slices[1], Pp / KB, np / 64, N_A * s))
       return HS_ECUDA;
     AtomsArgs& at = PA.at;
     at.mA = 0;
@@ -1003,11 +1054,9 @@ int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const
     PA.N_G = N_G;
     PA.rows_pad = rp;
     PA.err = err_d;
-    int rc = set_smem((const void*)k_split_gemm<MODE_ATOMS>, smem);
-    if (rc) return rc;
     const int grid = at.ngblk * at.ntile * 2 * N_A;
-    k_split_gemm<MODE_ATOMS><<<grid, NUM_THREADS, smem, st>>>(PA);
-    HS_CUDA_TRY(cudaGetLastError());
+    int rc = launch_gemm(MODE_ATOMS, s, grid, smem, st, PA);
+    if (rc) return rc;
   }
   HS_CUDA_TRY(hs_launch_gather_af(A, ldAB, fail_list_d, N_f, N_L, N_G, w.AF, st));
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[4], st));
@@ -1035,10 +1084,10 @@ int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const
   auto add_map = [&](int src, int nblk) -> bool {
     SliceBuf& b = w.sb[src];
     map_of[src][0] = nm;
-    if (!encode_map(&P.maps[nm++], b.plain, nblk * Pp, s * rp)) return false;
+    if (!encode_tiles(&P.maps[nm++], b.plain, nblk * Pp / KB, rp / 64, s)) return false;
     if (b.rot) {
       map_of[src][1] = nm;
-      if (!encode_map(&P.maps[nm++], b.rot, nblk * Pp, s * rp)) return false;
+      if (!encode_tiles(&P.maps[nm++], b.rot, nblk * Pp / KB, rp / 64, s)) return false;
     }
     return true;
   };
@@ -1054,8 +1103,6 @@ int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const
   P.nbj = (N_G + BNC - 1) / BNC;
   P.rows_pad = rp;
   P.err = err_d;
-  int rc = set_smem((const void*)k_split_gemm<MODE_CONTRACT>, smem);
-  if (rc) return rc;
   const int nbi = (N_G + BM - 1) / BM;
   int tiles = 0;
   for (int b = 0; b < nbi; ++b) tiles += std::min(2 * b + 2, P.nbj);
@@ -1074,8 +1121,8 @@ int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const
   P.seg[0] = seg(SRC_A, SRC_A, N_A);
   P.seg[1] = seg(SRC_UB, SRC_UB, N_A);
   P.C = S;
-  k_split_gemm<MODE_CONTRACT><<<tiles, NUM_THREADS, smem, st>>>(P);
-  HS_CUDA_TRY(cudaGetLastError());
+  int rc = launch_gemm(MODE_CONTRACT, s, tiles, smem, st, P);
+  if (rc) return rc;
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[6], st));
   // H = Z^H B + B^H Z + Y^H Y + A_f^H X_f
   int n = 0;
@@ -1085,8 +1132,8 @@ int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const
   if (N_f > 0) P.seg[n++] = seg(SRC_AF, SRC_X, N_f);
   P.nseg = n;
   P.C = H;
-  k_split_gemm<MODE_CONTRACT><<<tiles, NUM_THREADS, smem, st>>>(P);
-  HS_CUDA_TRY(cudaGetLastError());
+  rc = launch_gemm(MODE_CONTRACT, s, tiles, smem, st, P);
+  if (rc) return rc;
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[7], st));
   return HS_OK;
 }
