@@ -153,6 +153,102 @@ def run_reference(args, w):
     return 0
 
 
+def run_serve(args):
+    """Serving: Poisson k-point requests through hs_submit / hs_poll (continuous batching).
+
+    Workload: N_A=64, N_L=81 (l_max = 8), N_G uniform in [1500, 9000] per request,
+    A and B column-truncated views of a pool of device-resident N_G=9000 sets
+    (seeded torch draws with the synth recipe's distributions), T and U shared by
+    all requests, admission by a 150 GB HBM budget.  --rate 0: every request at
+    t = 0 (saturation, k-points/s); --rate r: exponential inter-arrivals with mean
+    1/r s.  Latency = submit to GPU completion (host clock, reported by hs_poll).
+    """
+    import torch
+    from paper_1611_00606_gb300 import hs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    N_A, N_L, NGmax = 64, 81, 9000
+    K = N_A * N_L
+    rng = np.random.default_rng(args.seed)
+    sizes = rng.integers(1500, 9001, size=args.requests)
+    gaps = (rng.exponential(1.0 / args.rate, size=args.requests) if args.rate > 0
+            else np.zeros(args.requests))
+    arrivals = np.cumsum(gaps)
+    g = torch.Generator(device=dev).manual_seed(args.seed)
+    lscale = torch.tensor(1.0 / (1.0 + synth.l_of_L(N_L)), device=dev).repeat(N_A)
+
+    def coef():
+        x = torch.randn((NGmax, K), generator=g, device=dev, dtype=torch.complex128)
+        return (x * lscale[None, :]).T  # (K, N_G) column-major; complex randn has E|z|^2 = 1
+    pool = [(coef(), coef()) for _ in range(args.pool)]
+    T_AA, T_AB, T_BB = synth.t_matrices(N_A, N_L, synth.indefinite_atoms(N_A, 0.05), args.seed)
+    T = [hs.to_device_T(t, dev) for t in (T_AA, T_AB, T_BB)]
+    U = hs.to_device_U(synth.u_norms(N_A, N_L, args.seed), dev)
+    # the client owns H, S: a fixed set of reusable output buffers bounds its memory;
+    # an arrived request waits client-side for a free buffer pair (counted in latency)
+    nbuf = args.outstanding
+    bufs = [(torch.empty(NGmax * NGmax, dtype=torch.complex128, device=dev),
+             torch.empty(NGmax * NGmax, dtype=torch.complex128, device=dev)) for _ in range(nbuf)]
+    free = list(range(nbuf))
+
+    def view(b, n):  # column-major (n, n) view of a buffer's first n*n entries
+        return b[: n * n].view(n, n).T
+    plan = hs.hs_plan(N_A, N_L, NGmax, args.precision,
+                      args.slices if args.precision == "split_bf16" else 0, 150 * 10 ** 9)
+    hs.hs_set_t(plan, *T)
+    for n in (1500, NGmax):  # warm-up: one request of each extreme size
+        t = hs.hs_submit(plan, pool[0][0], pool[0][1], U, n, view(bufs[0][0], n),
+                         view(bufs[0][1], n))
+        hs.hs_poll(plan, t, -1)
+    torch.cuda.synchronize()
+    inflight = []   # (ticket, request index, buffer index)
+    submit_t = {}
+    done = {}
+    t0 = time.perf_counter()
+    i = 0
+    while len(done) < args.requests:
+        now = time.perf_counter() - t0
+        while i < args.requests and arrivals[i] <= now and free:
+            n = int(sizes[i])
+            bi = free.pop()
+            A, B = pool[i % args.pool]
+            t = hs.hs_submit(plan, A, B, U, n, view(bufs[bi][0], n), view(bufs[bi][1], n))
+            submit_t[i] = time.perf_counter() - t0
+            inflight.append((t, i, bi))
+            i += 1
+        for rec in list(inflight):
+            rc, info = hs.hs_poll(plan, rec[0], 0)
+            if rc == hs.HS_OK:
+                done[rec[1]] = info
+                inflight.remove(rec)
+                free.append(rec[2])
+        time.sleep(0.0002)
+    wall = time.perf_counter() - t0
+    hs.hs_destroy(plan)
+    # latency: arrival -> GPU completion (client wait for a buffer + queue + run)
+    lat = np.array([1e3 * (submit_t[j] - arrivals[j]) + done[j]["ms_latency"]
+                    for j in range(args.requests)])
+    que = np.array([1e3 * (submit_t[j] - arrivals[j]) + done[j]["ms_queue"]
+                    for j in range(args.requests)])
+    F = sum(_flops.assembly_flops(N_A, N_L, int(n), len(synth.indefinite_atoms(N_A, 0.05)))
+            for n in sizes)
+    out = {"metric": "serving k-points/s and p50/p99 latency", "mode": "serve",
+           "precision": args.precision, "slices": args.slices if args.precision == "split_bf16"
+           else 0, "requests": args.requests,
+           "rate_per_s": args.rate if args.rate > 0 else "saturation",
+           "kpts_per_s": args.requests / wall, "tflops": F / wall / 1e12, "wall_s": wall,
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean()), "max": float(lat.max())},
+           "queue_ms": {"p50": float(np.percentile(que, 50)), "p99": float(np.percentile(que, 99))},
+           "max_inflight_gb": max(done[j]["inflight_bytes"] for j in done) / 1e9,
+           "config": {"workload": "serving: N_A=64, N_L=81, N_G ~ U[1500, 9000], T shared, "
+                                  f"pool of {args.pool} N_G=9000 A/B sets, budget 150 GB, "
+                                  f"{args.outstanding} client H/S buffer pairs",
+                      "seed": args.seed}}
+    print(json.dumps(out))
+    return 0
+
+
 def _wl_desc(w):
     return (f"{w.name} (N_A={w.N_A}, N_L={w.N_L}, N_G={w.N_G}, "
             f"{len(w.indefinite)} indefinite T_AA)")
@@ -171,7 +267,15 @@ def main():
     ap.add_argument("--ref-cols", type=int, default=48, help="oracle panel width per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="serving benchmark (hs_submit/hs_poll)")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=0.0, help="Poisson arrivals per s (0: all at t=0)")
+    ap.add_argument("--pool", type=int, default=4)
+    ap.add_argument("--outstanding", type=int, default=24, help="client output buffer pairs")
+    ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
+    if args.serve:
+        return run_serve(args)
     w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)

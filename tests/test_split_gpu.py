@@ -113,3 +113,52 @@ def test_split_paper_scale_panels(hs):
     print(f"auag_like_4000 split s=5: H {eh:.3e} S {es:.3e}")
     assert eh <= TOL_SPLIT and es <= TOL_SPLIT
     assert list(np.nonzero(flags)[0]) == list(w.indefinite)
+
+
+def test_error_table_split_8000(hs):
+    """split_8000 (N_A=100, N_L=121, N_G=8000): max relative Frobenius error of H, S
+    on oracle column panels for every slice count; the default (5) meets 1e-10.
+
+    Each slice adds 9 bits until s = 5; from s = 6 on the error levels off near
+    5e-12: slice levels >= 3 share one inexact FP32 accumulator per 128-wide K
+    window, and the tensor core's truncating FP32 additions leave ~2^-36 of
+    relative error per window at this K (about 600 windows per contraction)."""
+    w = synth.WORKLOADS["split_8000"]
+    d = synth.make_inputs(w)
+    cols = _panel_cols(w.N_G)
+    Hr, Sr = assemble(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], w.N_A, w.N_L,
+                      cols=cols)
+    A, B = hs.to_device_coef(d["A"]), hs.to_device_coef(d["B"])
+    T = [hs.to_device_T(d[k]) for k in ("T_AA", "T_AB", "T_BB")]
+    U = hs.to_device_U(d["U"])
+    table = {}
+    for s in range(2, 8):
+        with hs.Plan(w.N_A, w.N_L, w.N_G, "split_bf16", s) as p:
+            H, S, info = p.assemble(A, B, *T, U)
+            torch.cuda.synchronize()
+            table[s] = (rel_frobenius(H[:, cols].cpu().numpy(), Hr),
+                        rel_frobenius(S[:, cols].cpu().numpy(), Sr), info["ms_total"])
+        del H, S
+    print("\nsplit_8000 error table (slices: H, S, ms):")
+    for s, (eh, es, ms) in table.items():
+        print(f"  s={s}: H {eh:.3e}  S {es:.3e}  {ms:.1f} ms")
+    assert max(table[5][:2]) <= TOL_SPLIT
+    for s in (2, 3, 4):
+        assert max(table[s + 1][:2]) < max(table[s][:2]) / 16
+    assert max(max(table[s][:2]) for s in (6, 7)) <= min(1e-11, max(table[5][:2]))
+
+
+def test_split_large_12000_panels(hs):
+    """large_12000 (N_A=256, N_L=144, N_G=12000, 5 indefinite): the largest shape, on
+    oracle column panels at the start, middle and end."""
+    w = synth.WORKLOADS["large_12000"]
+    d = synth.make_inputs(w)
+    H, S, info, flags = _run(hs, d, w.N_A, w.N_L)
+    cols = _panel_cols(w.N_G)
+    Hr, Sr = assemble(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], w.N_A, w.N_L,
+                      cols=cols)
+    eh, es = rel_frobenius(H[:, cols], Hr), rel_frobenius(S[:, cols], Sr)
+    print(f"large_12000 split s=5: H {eh:.3e} S {es:.3e}  {info['ms_total']:.1f} ms")
+    assert eh <= TOL_SPLIT and es <= TOL_SPLIT
+    assert list(np.nonzero(flags)[0]) == list(w.indefinite)
+    assert np.array_equal(H[:, cols].conj().T[:, cols], H[np.ix_(cols, cols)])
