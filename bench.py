@@ -116,6 +116,17 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_max(x: float, dev) -> float:
+    """Max of a host scalar over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, w):
     """CPU FP64 oracle on a bounded column panel per step (rank 0 only)."""
     ws, rank, _ = _dist()
@@ -324,13 +335,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return reduce_max(e0.elapsed_time(e1), dev)
 
     # ---------------- main form (device-resident inputs)
     plan = hs.hs_plan(w.N_A, w.N_L, w.N_G, args.precision, args.slices if
@@ -410,11 +415,7 @@ def main():
         torch.cuda.synchronize()
         t_e = time.perf_counter() - t0
         hs.hs_destroy(ph)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([t_e], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e = float(t.item())
+        t_e = reduce_max(t_e, dev)
         h2d = 16 * K * w.N_G * 2 + 8 * K + 3 * 16 * w.N_A * w.N_L * w.N_L
         e2e = {"value": F * ws * e_steps / t_e / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 2 * 16 * w.N_G * w.N_G, "steps": e_steps,
