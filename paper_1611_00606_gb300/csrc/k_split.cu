@@ -174,56 +174,26 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 }
 
 
-// Drain 16 TMEM columns (one strip of this warp) of accumulator group G into
-// (hi, lo) pairs kept in units of the current segment's scale 2^(E_row + E_col).
-// Groups 0-2 hold exact integer window sums and go through an error-free TwoSum
-// into hi; group 3 (levels >= 3) is added to lo.
-template <int G>
-__device__ __forceinline__ void drain_group(uint32_t taddr, float (&hi)[16], float (&lo)[16]) {
-  float v[16];
-  float (&v0)[4] = *reinterpret_cast<float(*)[4]>(&v[0]);
-  float (&v1)[4] = *reinterpret_cast<float(*)[4]>(&v[4]);
-  float (&v2)[4] = *reinterpret_cast<float(*)[4]>(&v[8]);
-  float (&v3)[4] = *reinterpret_cast<float(*)[4]>(&v[12]);
-  const uint32_t base = taddr + G * BN;
-  tmem_ld4(base, v0);
-  tmem_ld4(base + 4, v1);
-  tmem_ld4(base + 8, v2);
-  tmem_ld4(base + 12, v3);
-  tmem_wait_ld();
+// Drain 16 TMEM columns of the four window accumulators (level k at column
+// offset k*BN) into (hi, lo) pairs kept in units of the current segment's
+// scale 2^(E_row + E_col): the window sums are exact integers (levels 0-2), so
+// levels 0, 1, 2 go through an error-free TwoSum into hi and levels >= 3 into lo.
+__device__ __forceinline__ void drain16(uint32_t taddr, int s, float (&hi)[16], float (&lo)[16]) {
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    if (G < 3) two_sum_acc(hi[c], lo[c], v[c]);
-    else lo[c] += v[c];
-  }
-}
-
-// Read out group G of a finished window (strip 0, then strip 1), then release it.
-template <int G>
-__device__ __forceinline__ void drain_release(uint32_t tl, float (&h0)[16], float (&l0)[16],
-                                              float (&h1)[16], float (&l1)[16], uint64_t* rel,
-                                              int lane) {
-  drain_group<G>(tl, h0, l0);
-  float v[16];
-  {
-    float (&v0)[4] = *reinterpret_cast<float(*)[4]>(&v[0]);
-    float (&v1)[4] = *reinterpret_cast<float(*)[4]>(&v[4]);
-    float (&v2)[4] = *reinterpret_cast<float(*)[4]>(&v[8]);
-    float (&v3)[4] = *reinterpret_cast<float(*)[4]>(&v[12]);
-    const uint32_t base = tl + (uint32_t)BNC + G * BN;
-    tmem_ld4(base, v0);
-    tmem_ld4(base + 4, v1);
-    tmem_ld4(base + 8, v2);
-    tmem_ld4(base + 12, v3);
+  for (int c0 = 0; c0 < 16; c0 += 4) {
+    float v0[4], v1[4], v2[4], v3[4];
+    tmem_ld4(taddr + c0, v0);
+    tmem_ld4(taddr + BN + c0, v1);
+    if (s >= 3) tmem_ld4(taddr + 2 * BN + c0, v2);
+    if (s >= 4) tmem_ld4(taddr + 3 * BN + c0, v3);
     tmem_wait_ld();
-  }
-  tc_fence_before();
-  __syncwarp();
-  if (lane == 0) mbar_arrive(rel);  // the MMA thread may now restart this accumulator
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    if (G < 3) two_sum_acc(h1[c], l1[c], v[c]);
-    else l1[c] += v[c];
+    for (int c = 0; c < 4; ++c) {
+      two_sum_acc(hi[c0 + c], lo[c0 + c], v0[c]);
+      two_sum_acc(hi[c0 + c], lo[c0 + c], v1[c]);
+      if (s >= 3) two_sum_acc(hi[c0 + c], lo[c0 + c], v2[c]);
+      if (s >= 4) lo[c0 + c] += v3[c];
+    }
   }
 }
 
@@ -392,25 +362,6 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t ad0, uint64_
   }
 }
 
-// The pairs of one accumulator group G (level G for G < 3, levels >= 3 for
-// G == 3) of a stage, the group's lead pair overwriting (first stage of a window).
-template <int S, int G>
-__device__ __forceinline__ void issue_group(uint32_t tmem, uint64_t ad0, uint64_t bd0, bool init) {
-#pragma unroll
-  for (int p = 0; p < S; ++p) {
-#pragma unroll
-    for (int q = 0; q < S - p; ++q) {
-      constexpr int kStep = (2 * TILE_BYTES) >> 4;
-      const int lvl = p + q;
-      const int acc = lvl < 3 ? lvl : 3;
-      if (acc != G) continue;
-      const bool lead = (p == 0 && q == acc);
-      tc_mma_bf16(tmem + acc * BN, ad0 + (uint64_t)(p * kStep), bd0 + (uint64_t)(q * kStep), kIdesc,
-                  (lead && init) ? 0u : 1u);
-    }
-  }
-}
-
 template <int MODE, int S>
 __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_constant__ SplitParams P) {
   extern __shared__ uint8_t smem_raw[];
@@ -424,8 +375,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   uint64_t* full = (uint64_t*)(smem + ring_bytes);
   uint64_t* empty = full + NS;
   uint64_t* acc_full = empty + NS;
-  uint64_t* acc_empty = acc_full + 1;  // [4]: one release barrier per accumulator
-  uint64_t* done = acc_empty + 4;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* done = acc_empty + 1;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -437,7 +388,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
       mbar_init(&empty[i], 1);
     }
     mbar_init(acc_full, 1);
-    for (int a = 0; a < 4; ++a) mbar_init(&acc_empty[a], NUM_DRAIN_WARPS);
+    mbar_init(acc_empty, NUM_DRAIN_WARPS);
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -518,6 +469,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
       for (int sg = 0; sg < T.nseg && ok; ++sg) {
         const int kbn = seg_info<MODE>(P, T, sg).kblocks;
         for (int w0 = 0; w0 < kbn && ok; w0 += WIN) {
+          if (nwin > 0 && !mbar_wait(acc_empty, (uint32_t)(nwin - 1) & 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
           const int w1 = min(kbn, w0 + WIN);
           for (int kb = w0; kb < w1; ++kb) {
             if (!mbar_wait(&full[slot], phase, abort_flag)) {
@@ -526,31 +482,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
             }
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + slot * stage_bytes);
-            const uint64_t ad0 = sdesc_sw32(sa), bd0 = sdesc_sw32(sa + a_bytes);
-            if (kb == w0) {
-              // restart the accumulators in the order the drain releases them
-              // (levels >= 3 first, level 0 last), so the tensor pipe has work
-              // while the rest of the previous window is still being read out
-              const uint32_t par = (uint32_t)(nwin - 1) & 1u;
-              if (S >= 4) {
-                if (nwin > 0 && !(ok = mbar_wait(&acc_empty[3], par, abort_flag))) break;
-                tc_fence_after();
-                issue_group<S, 3>(tmem, ad0, bd0, true);
-              }
-              if (S >= 3) {
-                if (nwin > 0 && !(ok = mbar_wait(&acc_empty[2], par, abort_flag))) break;
-                tc_fence_after();
-                issue_group<S, 2>(tmem, ad0, bd0, true);
-              }
-              if (nwin > 0 && !(ok = mbar_wait(&acc_empty[1], par, abort_flag))) break;
-              tc_fence_after();
-              issue_group<S, 1>(tmem, ad0, bd0, true);
-              if (nwin > 0 && !(ok = mbar_wait(&acc_empty[0], par, abort_flag))) break;
-              tc_fence_after();
-              issue_group<S, 0>(tmem, ad0, bd0, true);
-            } else {
-              issue_stage<S>(tmem, ad0, bd0, false);
-            }
+            issue_stage<S>(tmem, sdesc_sw32(sa), sdesc_sw32(sa + a_bytes), kb == w0);
             tc_commit(&empty[slot]);
             if (++slot == NS) {
               slot = 0;
@@ -608,10 +540,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           break;
         }
         tc_fence_after();
-        if (S >= 4) drain_release<3>(tl, h0, l0, h1, l1, &acc_empty[3], lane);
-        if (S >= 3) drain_release<2>(tl, h0, l0, h1, l1, &acc_empty[2], lane);
-        drain_release<1>(tl, h0, l0, h1, l1, &acc_empty[1], lane);
-        drain_release<0>(tl, h0, l0, h1, l1, &acc_empty[0], lane);
+        drain16(tl, s, h0, l0);
+        drain16(tl + (uint32_t)BNC, s, h1, l1);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);
         ++nwin;
       }
     }
