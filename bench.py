@@ -45,6 +45,12 @@ METRIC = "H+S assembly TFLOP/s (Algorithm 1 flop count) per k-point, split-preci
 UNIT = "TFLOP/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+# DRAM bytes (read + write) of one H-contraction launch on auag_like_4000, split s = 5,
+# from ncu (profiles/k_split_gemm_contract_H_auag_like_4000_traffic.md), valid only
+# while the kernel source is the one measured (first 16 hex digits of its sha256).
+MEASURED_TRAFFIC = {"kernel_src_sha256": "809bb89e43d57026", "workload": "auag_like_4000", "slices": 5,
+                    "bytes": 63553965824 + 135893760}
+KERNEL_SRC = os.path.join(ROOT, "paper_1611_00606_gb300", "csrc", "k_split.cu")
 
 
 def _peaks():
@@ -275,7 +281,10 @@ def main():
     ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp64"])
     ap.add_argument("--slices", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the FP64 form (0: skip)")
-    ap.add_argument("--ref-cols", type=int, default=48, help="oracle panel width per step")
+    ap.add_argument("--ref-cols", type=int, default=48,
+                    help="oracle panel width per step of --impl reference")
+    ap.add_argument("--cpu-cols", type=int, default=512,
+                    help="oracle panel width of the cpu_baseline sample (about 10 s of CPU work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve", action="store_true", help="serving benchmark (hs_submit/hs_poll)")
@@ -361,8 +370,15 @@ def main():
         pairs = s * (s + 1) // 2
         achieved = pairs * F_H / (ms_H / 1e3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-        roof = {"bound": "tensor", "kernel": "k_contract_split (H)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+        import hashlib
+        with open(KERNEL_SRC, "rb") as f:
+            src = hashlib.sha256(f.read()).hexdigest()[:16]
+        traffic = (MEASURED_TRAFFIC["bytes"] if src == MEASURED_TRAFFIC["kernel_src_sha256"]
+                   and w.name == MEASURED_TRAFFIC["workload"]
+                   and s == MEASURED_TRAFFIC["slices"] else None)
+        roof = {"bound": "tensor", "kernel": "k_split_gemm<MODE_CONTRACT> (H)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "work": f"{pairs} slice pairs x Algorithm 1 flops of H1+H2+H3 (BF16 tensor)",
                 "peak_source": f"bf16_tflops_sustained ({peak_src})"}
     else:
@@ -426,7 +442,7 @@ def main():
     err = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import assemble, rel_frobenius
-        ncols = args.ref_cols
+        ncols = min(args.cpu_cols, w.N_G)
         cols = np.arange(ncols)
         t0 = time.perf_counter()
         Hr, Sr = assemble(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], w.N_A,
