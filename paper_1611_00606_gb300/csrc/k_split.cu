@@ -43,7 +43,8 @@ constexpr int BN = 2 * BNC;    // MMA N (Re | Im)
 constexpr int KB = 16;         // real K per pipeline stage (= one MMA K step)
 constexpr int WIN = 8;         // stages per exact window (128 real K)
 constexpr int ROWS_ALIGN = 128;
-constexpr int kMaxMaps = 13;
+constexpr int kMaxBatch = 16;                 // requests per grouped per-atom launch
+constexpr int kMaxMaps = 2 + 2 * kMaxBatch;   // >= 13 for a contraction
 constexpr int kMaxJobs = 7;
 constexpr int TILE_BYTES = 64 * KB * 2;  // one 64-row TMA box: 2 KB
 constexpr int NUM_DRAIN_WARPS = 16;     // four per TMEM lane quarter
@@ -226,18 +227,27 @@ struct SplitSeg {
   const int* eR;    // exponents of the R source columns
 };
 
-struct AtomsArgs {
-  int mA, mB;             // coefficient slice maps (plain)
-  int mOp[2];             // operator slice maps: [0] Z job, [1] W2 job
-  const int* eA;          // column exponents of A, B
+// One request of a grouped per-atom launch.
+struct AtomsReq {
+  int mA, mB;         // coefficient slice maps (plain) of this request
+  const int* eA;      // column exponents of its A, B slices
   const int* eB;
+  double2* Z;         // outputs, column-major, leading dimension AtomsArgs::ld
+  double2* W2;
+  int N_G;
+  int ngblk;          // 128-row blocks of G
+  int tile0;          // first CTA index of this request in the grouped grid
+};
+
+struct AtomsArgs {
+  AtomsReq rq[kMaxBatch];
+  int nreq;
+  int mOp[2];             // operator slice maps: [0] Z job, [1] W2 job (shared by requests)
   const int* eOp[2];      // operator row exponents [a][n_pad]
   const int* slot;        // W2 slot of each atom
-  double2* Z;             // outputs, column-major, leading dimension ld
-  double2* W2;
   int ld;
   int N_A, N_L, P;        // P: padded real K of one atom block (multiple of KB)
-  int n_pad, ntile, ngblk;
+  int n_pad, ntile;
 };
 
 struct __align__(64) SplitParams {
@@ -270,6 +280,8 @@ struct SegInfo {
 struct TileId {
   int i0, j0;      // CONTRACT: row / column origin
   int a, job, n0;  // ATOMS: atom, job (0: Z, 1: W2), operator row origin (i0 = g origin)
+  int r;           // ATOMS: request of the grouped launch
+  int N_G;         // columns of the (request's) output
   int nseg;
 };
 
@@ -287,10 +299,16 @@ __device__ __forceinline__ TileId decode_tile(const SplitParams& P) {
     t.i0 = bi * BM;
     t.j0 = b * BNC;
     t.nseg = P.nseg;
+    t.N_G = P.N_G;
   } else {
-    int b = blockIdx.x;
-    const int gb = b % P.at.ngblk;
-    b /= P.at.ngblk;
+    int r = 0;
+    while (r + 1 < P.at.nreq && (int)blockIdx.x >= P.at.rq[r + 1].tile0) ++r;
+    const AtomsReq& R = P.at.rq[r];
+    int b = blockIdx.x - R.tile0;
+    t.r = r;
+    t.N_G = R.N_G;
+    const int gb = b % R.ngblk;
+    b /= R.ngblk;
     const int nt = b % P.at.ntile;
     b /= P.at.ntile;
     t.job = b & 1;
@@ -323,7 +341,8 @@ __device__ __forceinline__ SegInfo seg_info(const SplitParams& P, const TileId& 
     si.eC1 = S.eR + t.j0;
   } else {
     const AtomsArgs& A = P.at;
-    si.mL = &P.maps[sg == 0 ? A.mA : A.mB];
+    const AtomsReq& R = A.rq[t.r];
+    si.mL = &P.maps[sg == 0 ? R.mA : R.mB];
     si.mR1 = si.mR2 = &P.maps[A.mOp[t.job]];
     si.kbL = t.a * (A.P / KB);
     si.rbL = t.i0 >> 6;
@@ -333,7 +352,7 @@ __device__ __forceinline__ SegInfo seg_info(const SplitParams& P, const TileId& 
     si.rbR2 = (t.n0 >> 6) + 1;
     si.plR = t.a * P.s;
     si.kblocks = A.P / KB;
-    si.eRow = sg == 0 ? A.eA : A.eB;
+    si.eRow = sg == 0 ? R.eA : R.eB;
     si.eC0 = A.eOp[t.job] + t.a * A.n_pad + t.n0;
     si.eC1 = si.eC0 + 64;
   }
@@ -586,13 +605,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
         }
       } else {
         const AtomsArgs& A = P.at;
-        double2* out = T.job == 0 ? A.Z + (size_t)T.a * A.N_L
-                                  : A.W2 + (size_t)A.slot[T.a] * A.N_L;
+        const AtomsReq& R = A.rq[T.r];
+        double2* out = T.job == 0 ? R.Z + (size_t)T.a * A.N_L
+                                  : R.W2 + (size_t)A.slot[T.a] * A.N_L;
         const int Lb = T.n0 >> 1;
         for (int idx = dt; idx < 64 * 128; idx += 32 * NUM_DRAIN_WARPS) {
           const int gg = idx >> 6, ll = idx & 63;  // tile row, local output row
           const int g = T.i0 + gg, L = Lb + ll;
-          if (g < P.N_G && L < A.N_L) {
+          if (g < T.N_G && L < A.N_L) {
             const int nl = 2 * ll, st = nl >> 6, c = nl & 63;
             const float2 re = stg[(st * 64 + c) * 128 + gg], im = stg[(st * 64 + c + 1) * 128 + gg];
             const double sre = pow2d(s_erow[gg] + s_ecol[st * 64 + c]);
@@ -974,110 +994,191 @@ static int launch_gemm(int mode, int s, int grid, size_t smem, cudaStream_t st,
                                : launch_mode<MODE_ATOMS>(s, grid, smem, st, P);
 }
 
-int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const double* U,
-                             int N_G, double2* H, double2* S, Workspace& w, cudaStream_t st,
-                             bool timed) {
+static const void* atoms_fn(int s) {
+  switch (s) {
+    case 2: return (const void*)k_split_gemm<MODE_ATOMS, 2>;
+    case 3: return (const void*)k_split_gemm<MODE_ATOMS, 3>;
+    case 4: return (const void*)k_split_gemm<MODE_ATOMS, 4>;
+    case 5: return (const void*)k_split_gemm<MODE_ATOMS, 5>;
+    case 6: return (const void*)k_split_gemm<MODE_ATOMS, 6>;
+    case 7: return (const void*)k_split_gemm<MODE_ATOMS, 7>;
+    default: return nullptr;
+  }
+}
+
+// The grouped per-atom launch as the single kernel node of a CUDA graph:
+// captured once per plan, then re-parameterised (cudaGraphExecKernelNodeSetParams:
+// grid and arguments of this batch) and replayed for every batch.  Updates only
+// affect later launches, so a replay still running is undisturbed.
+struct AtomsGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t node = nullptr;
+};
+
+AtomsGraph* hs_atoms_graph_new() { return new (std::nothrow) AtomsGraph(); }
+void hs_atoms_graph_free(AtomsGraph* a) {
+  if (!a) return;
+  if (a->exec) cudaGraphExecDestroy(a->exec);
+  if (a->g) cudaGraphDestroy(a->g);
+  delete a;
+}
+
+static int graph_launch_atoms(AtomsGraph& G, int s, int grid, size_t smem, cudaStream_t st,
+                              const SplitParams& P) {
+  const void* fn = atoms_fn(s);
+  if (!fn) return HS_EINVAL;
+  int rc = set_smem(fn, smem);
+  if (rc) return rc;
+  void* args[1] = {(void*)&P};
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof(kp));
+  kp.func = (void*)fn;
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(NUM_THREADS);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = args;
+  if (!G.exec) {
+    HS_CUDA_TRY(cudaGraphCreate(&G.g, 0));
+    HS_CUDA_TRY(cudaGraphAddKernelNode(&G.node, G.g, nullptr, 0, &kp));
+    HS_CUDA_TRY(cudaGraphInstantiate(&G.exec, G.g, 0));
+  } else {
+    HS_CUDA_TRY(cudaGraphExecKernelNodeSetParams(G.exec, G.node, &kp));
+  }
+  HS_CUDA_TRY(cudaGraphLaunch(G.exec, st));
+  return HS_OK;
+}
+
+int hs_plan_s::split_geometry(int& n_stage, size_t& smem) const {
+  const int stage_bytes = 4 * slices * TILE_BYTES;
+  const int budget = 227 * 1024 - 1024 - 256;
+  n_stage = budget / stage_bytes;
+  if (n_stage > 8) n_stage = 8;
+  if (n_stage < 2) return HS_EINVAL;
+  smem = std::max((size_t)n_stage * stage_bytes, (size_t)STAGING_BYTES) + 1024 + 256;
+  return HS_OK;
+}
+
+static void slice_job(SliceParams& sp, int& nj, Workspace& w, int src, const double2* X, int ldX,
+                      int nblk, const double* u) {
+  SliceBuf& b = w.sb[src];
+  sp.job[nj++] = SliceJob{X, u, b.plain, b.rot, b.expo, ldX, nblk};
+}
+
+static int slice_launch(SliceParams& sp, int nj, int s, int N_G, int rp, int N_L, int Pp,
+                        cudaStream_t st) {
+  sp.s = s;
+  sp.N_G = N_G;
+  sp.rows_pad = rp;
+  sp.N_L = N_L;
+  sp.P = Pp;
+  k_slice<<<dim3(rp, nj), 256, 0, st>>>(sp);
+  return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
+}
+
+// 1. slice the inputs A, U.B, B of one k-point
+int hs_plan_s::split_inputs(const double2* A, const double2* B, int ldAB, const double* U,
+                            int N_G, Workspace& w, cudaStream_t st) {
+  const int rp = rows_pad_of(N_G);
+  if (rows_pad_of(w.N_G) < rp || w.n_fail < N_f || !w.sb[SRC_A].plain) return HS_EINVAL;
+  SliceParams sp{};
+  int nj = 0;
+  slice_job(sp, nj, w, SRC_A, A, ldAB, N_A, nullptr);
+  slice_job(sp, nj, w, SRC_UB, B, ldAB, N_A, U);
+  slice_job(sp, nj, w, SRC_B, B, ldAB, N_A, nullptr);
+  return slice_launch(sp, nj, slices, N_G, rp, N_L, block_pad(N_L), st);
+}
+
+// 2. per-atom products of up to kMaxBatch k-points in one grouped launch: Z and
+//    W2 = [Y; X] in FP64.  With `graph`, the launch is the (re-parameterised) kernel
+//    node of the plan's captured graph.
+int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGraph* graph) {
+  if (n < 1 || n > kMaxBatch) return HS_EINVAL;
+  const int s = slices, Pp = block_pad(N_L), np = op_rows_pad(N_L);
+  int n_stage;
+  size_t smem;
+  int rc = split_geometry(n_stage, smem);
+  if (rc) return rc;
+  SplitParams* PA = new (std::nothrow) SplitParams;
+  if (!PA) return HS_ENOMEM;
+  std::memset(PA, 0, sizeof(*PA));
+  AtomsArgs& at = PA->at;
+  bool ok = encode_tiles(&PA->maps[0], op_slices[0], 2 * Pp / KB, np / 64, N_A * s) &&
+            encode_tiles(&PA->maps[1], op_slices[1], Pp / KB, np / 64, N_A * s);
+  at.mOp[0] = 0;
+  at.mOp[1] = 1;
+  int grid = 0;
+  for (int r = 0; r < n && ok; ++r) {
+    Workspace& w = *jobs[r].w;
+    const int rp = rows_pad_of(jobs[r].N_G);
+    AtomsReq& R = at.rq[r];
+    R.mA = 2 + 2 * r;
+    R.mB = 3 + 2 * r;
+    ok = encode_tiles(&PA->maps[R.mA], w.sb[SRC_A].plain, N_A * Pp / KB, rp / 64, s) &&
+         encode_tiles(&PA->maps[R.mB], w.sb[SRC_B].plain, N_A * Pp / KB, rp / 64, s);
+    R.eA = w.sb[SRC_A].expo;
+    R.eB = w.sb[SRC_B].expo;
+    R.Z = w.Z;
+    R.W2 = w.W2;
+    R.N_G = jobs[r].N_G;
+    R.ngblk = rp / BM;
+    R.tile0 = grid;
+    grid += R.ngblk * (np / BN) * 2 * N_A;
+  }
+  if (!ok) {
+    delete PA;
+    return HS_ECUDA;
+  }
+  at.nreq = n;
+  at.eOp[0] = op_expo[0];
+  at.eOp[1] = op_expo[1];
+  at.slot = slot_d;
+  at.ld = N_A * N_L;
+  at.N_A = N_A;
+  at.N_L = N_L;
+  at.P = Pp;
+  at.n_pad = np;
+  at.ntile = np / BN;
+  PA->s = s;
+  PA->n_stage = n_stage;
+  PA->err = err_d;
+  rc = graph ? graph_launch_atoms(*graph, s, grid, smem, st, *PA)
+             : launch_gemm(MODE_ATOMS, s, grid, smem, st, *PA);
+  delete PA;
+  return rc;
+}
+
+// 3. gather A_f, slice the per-atom outputs, and the two stacked contractions
+int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, double2* S,
+                             Workspace& w, cudaStream_t st, bool timed) {
   const int K = N_A * N_L;
   const int N_h = N_A - N_f;
   const int s = slices;
   const int rp = rows_pad_of(N_G);
   const int Pp = block_pad(N_L);
-  const int np = op_rows_pad(N_L);
-  if (rows_pad_of(w.N_G) < rp || w.n_fail < N_f || !w.sb[SRC_A].plain) return HS_EINVAL;
-
-  // pipeline geometry shared by both kernel modes
-  const int stage_bytes = 4 * s * TILE_BYTES;
-  const int budget = 227 * 1024 - 1024 - 256;
-  int n_stage = budget / stage_bytes;
-  if (n_stage > 8) n_stage = 8;
-  if (n_stage < 2) return HS_EINVAL;
-  const size_t smem = std::max((size_t)n_stage * stage_bytes, (size_t)STAGING_BYTES) + 1024 + 256;
-
-  auto slice_launch = [&](SliceParams& sp, int nj) -> int {
-    sp.s = s;
-    sp.N_G = N_G;
-    sp.rows_pad = rp;
-    sp.N_L = N_L;
-    sp.P = Pp;
-    k_slice<<<dim3(rp, nj), 256, 0, st>>>(sp);
-    HS_CUDA_TRY(cudaGetLastError());
-    return HS_OK;
-  };
-  auto job = [&](SliceParams& sp, int& nj, int src, const double2* X, int ldX, int nblk,
-                 const double* u) {
-    SliceBuf& b = w.sb[src];
-    sp.job[nj++] = SliceJob{X, u, b.plain, b.rot, b.expo, ldX, nblk};
-  };
-
-  // 1. slice the inputs A, U.B, B
-  {
-    SliceParams sp{};
-    int nj = 0;
-    job(sp, nj, SRC_A, A, ldAB, N_A, nullptr);
-    job(sp, nj, SRC_UB, B, ldAB, N_A, U);
-    job(sp, nj, SRC_B, B, ldAB, N_A, nullptr);
-    int rc = slice_launch(sp, nj);
-    if (rc) return rc;
-  }
-  if (timed) HS_CUDA_TRY(cudaEventRecord(ev[9], st));
-
-  // 2. per-atom products on the tensor cores: Z and W2 = [Y; X] in FP64
-  {
-    SplitParams PA;
-    std::memset(&PA, 0, sizeof(PA));
-    if (!encode_tiles(&PA.maps[0], w.sb[SRC_A].plain, N_A * Pp / KB, rp / 64, s) ||
-        !encode_tiles(&PA.maps[1], w.sb[SRC_B].plain, N_A * Pp / KB, rp / 64, s) ||
-        !encode_tiles(&PA.maps[2], op_slices[0], 2 * Pp / KB, np / 64, N_A * s) ||
-        !encode_tiles(&PA.maps[3], op_slices[1], Pp / KB, np / 64, N_A * s))
-      return HS_ECUDA;
-    AtomsArgs& at = PA.at;
-    at.mA = 0;
-    at.mB = 1;
-    at.mOp[0] = 2;
-    at.mOp[1] = 3;
-    at.eA = w.sb[SRC_A].expo;
-    at.eB = w.sb[SRC_B].expo;
-    at.eOp[0] = op_expo[0];
-    at.eOp[1] = op_expo[1];
-    at.slot = slot_d;
-    at.Z = w.Z;
-    at.W2 = w.W2;
-    at.ld = K;
-    at.N_A = N_A;
-    at.N_L = N_L;
-    at.P = Pp;
-    at.n_pad = np;
-    at.ntile = np / BN;
-    at.ngblk = rp / BM;
-    PA.s = s;
-    PA.n_stage = n_stage;
-    PA.N_G = N_G;
-    PA.rows_pad = rp;
-    PA.err = err_d;
-    const int grid = at.ngblk * at.ntile * 2 * N_A;
-    int rc = launch_gemm(MODE_ATOMS, s, grid, smem, st, PA);
-    if (rc) return rc;
-  }
+  int n_stage;
+  size_t smem;
+  int rc = split_geometry(n_stage, smem);
+  if (rc) return rc;
   HS_CUDA_TRY(hs_launch_gather_af(A, ldAB, fail_list_d, N_f, N_L, N_G, w.AF, st));
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[4], st));
-
-  // 3. slice the per-atom outputs Z, Y, A_f, X
   {
     SliceParams sp{};
     int nj = 0;
-    job(sp, nj, SRC_Z, w.Z, K, N_A, nullptr);
-    if (N_h > 0) job(sp, nj, SRC_Y, w.W2, K, N_h, nullptr);
+    slice_job(sp, nj, w, SRC_Z, w.Z, K, N_A, nullptr);
+    if (N_h > 0) slice_job(sp, nj, w, SRC_Y, w.W2, K, N_h, nullptr);
     if (N_f > 0) {
-      job(sp, nj, SRC_AF, w.AF, N_f * N_L, N_f, nullptr);
-      job(sp, nj, SRC_X, w.W2 + (size_t)N_h * N_L, K, N_f, nullptr);
+      slice_job(sp, nj, w, SRC_AF, w.AF, N_f * N_L, N_f, nullptr);
+      slice_job(sp, nj, w, SRC_X, w.W2 + (size_t)N_h * N_L, K, N_f, nullptr);
     }
-    int rc = slice_launch(sp, nj);
+    rc = slice_launch(sp, nj, s, N_G, rp, N_L, Pp, st);
     if (rc) return rc;
   }
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[5], st));
 
-  // 4. the two stacked contractions
-  SplitParams P;
+  SplitParams* PP = new (std::nothrow) SplitParams;
+  if (!PP) return HS_ENOMEM;
+  SplitParams& P = *PP;
   std::memset(&P, 0, sizeof(P));
   int map_of[NSRC][2];
   int nm = 0;
@@ -1095,7 +1196,10 @@ int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const
             add_map(SRC_B, N_A);
   if (N_h > 0) ok = ok && add_map(SRC_Y, N_h);
   if (N_f > 0) ok = ok && add_map(SRC_AF, N_f) && add_map(SRC_X, N_f);
-  if (!ok) return HS_ECUDA;
+  if (!ok) {
+    delete PP;
+    return HS_ECUDA;
+  }
   P.s = s;
   P.n_stage = n_stage;
   P.N_G = N_G;
@@ -1121,19 +1225,32 @@ int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const
   P.seg[0] = seg(SRC_A, SRC_A, N_A);
   P.seg[1] = seg(SRC_UB, SRC_UB, N_A);
   P.C = S;
-  int rc = launch_gemm(MODE_CONTRACT, s, tiles, smem, st, P);
-  if (rc) return rc;
-  if (timed) HS_CUDA_TRY(cudaEventRecord(ev[6], st));
-  // H = Z^H B + B^H Z + Y^H Y + A_f^H X_f
-  int n = 0;
-  P.seg[n++] = seg(SRC_Z, SRC_B, N_A);
-  P.seg[n++] = seg(SRC_B, SRC_Z, N_A);
-  if (N_h > 0) P.seg[n++] = seg(SRC_Y, SRC_Y, N_h);
-  if (N_f > 0) P.seg[n++] = seg(SRC_AF, SRC_X, N_f);
-  P.nseg = n;
-  P.C = H;
   rc = launch_gemm(MODE_CONTRACT, s, tiles, smem, st, P);
+  if (rc == HS_OK && timed && cudaEventRecord(ev[6], st) != cudaSuccess) rc = HS_ECUDA;
+  if (rc == HS_OK) {
+    // H = Z^H B + B^H Z + Y^H Y + A_f^H X_f
+    int n = 0;
+    P.seg[n++] = seg(SRC_Z, SRC_B, N_A);
+    P.seg[n++] = seg(SRC_B, SRC_Z, N_A);
+    if (N_h > 0) P.seg[n++] = seg(SRC_Y, SRC_Y, N_h);
+    if (N_f > 0) P.seg[n++] = seg(SRC_AF, SRC_X, N_f);
+    P.nseg = n;
+    P.C = H;
+    rc = launch_gemm(MODE_CONTRACT, s, tiles, smem, st, P);
+    if (rc == HS_OK && timed && cudaEventRecord(ev[7], st) != cudaSuccess) rc = HS_ECUDA;
+  }
+  delete PP;
+  return rc;
+}
+
+int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const double* U,
+                             int N_G, double2* H, double2* S, Workspace& w, cudaStream_t st,
+                             bool timed) {
+  int rc = split_inputs(A, B, ldAB, U, N_G, w, st);
   if (rc) return rc;
-  if (timed) HS_CUDA_TRY(cudaEventRecord(ev[7], st));
-  return HS_OK;
+  if (timed) HS_CUDA_TRY(cudaEventRecord(ev[9], st));
+  AtomsJob job{&w, N_G};
+  rc = split_atoms(&job, 1, st, nullptr);
+  if (rc) return rc;
+  return split_outputs(A, ldAB, N_G, H, S, w, st, timed);
 }

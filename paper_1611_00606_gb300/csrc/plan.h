@@ -41,6 +41,14 @@ struct Workspace {
 };
 
 struct ServeState;  // serve.cu
+struct AtomsGraph;  // k_split.cu: graph holding the grouped per-atom launch
+AtomsGraph* hs_atoms_graph_new();
+void hs_atoms_graph_free(AtomsGraph* a);
+// One k-point of a grouped per-atom launch.
+struct AtomsJob {
+  Workspace* w;
+  int N_G;
+};
 struct hs_plan_s;
 // Stream-ordered pool for serving workspaces (null before the first hs_submit).
 cudaMemPool_t hs_serve_pool(hs_plan_s* p);
@@ -100,6 +108,12 @@ struct hs_plan_s {
               double2* S, Workspace& w, cudaStream_t st, bool timed);
   int split_enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G,
                     double2* H, double2* S, Workspace& w, cudaStream_t st, bool timed);
+  int split_geometry(int& n_stage, size_t& smem) const;
+  int split_inputs(const double2* A, const double2* B, int ldAB, const double* U, int N_G,
+                   Workspace& w, cudaStream_t st);
+  int split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGraph* graph);
+  int split_outputs(const double2* A, int ldAB, int N_G, double2* H, double2* S, Workspace& w,
+                    cudaStream_t st, bool timed);
   int check_device_error();
   void fill_info(hs_info* info, bool factored);
   bool serve_busy();

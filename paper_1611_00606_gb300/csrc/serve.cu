@@ -21,6 +21,8 @@
 
 namespace {
 
+constexpr int kAtomsBatchMax = 16;  // requests per grouped per-atom launch
+
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
       .count();
@@ -40,7 +42,7 @@ struct Request {
   double t_submit = 0, t_admit = 0;
   std::atomic<double> t_done{0.0};
   cudaStream_t st = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e_in = nullptr;
   Workspace ws;
   std::atomic<int> gpu_done{0};
   int state = 0;  // 0 queued, 1 running, 2 finished (resources returned)
@@ -63,6 +65,9 @@ struct ServeState {
   bool stop = false;
   std::thread th;
   cudaMemPool_t pool = nullptr;
+  cudaStream_t batch_stream = nullptr;  // grouped per-atom launches (split form)
+  AtomsGraph* graph = nullptr;
+  uint64_t batches = 0, batched_requests = 0;
   static constexpr int kMaxRunning = 16;
   static constexpr size_t kMaxQueue = 1u << 16;
 };
@@ -77,9 +82,7 @@ void CUDART_CB on_done(void* arg) {
   S->cv.notify_all();  // no CUDA calls and no locks in a host callback
 }
 
-// Launch one admitted request (called with S->mu held).
-int launch(ServeState* S, Request* r) {
-  hs_plan_s* p = S->plan;
+int take_stream(ServeState* S, Request* r) {
   if (S->free_streams.empty()) {
     cudaStream_t st;
     HS_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -90,17 +93,89 @@ int launch(ServeState* S, Request* r) {
   HS_CUDA_TRY(cudaEventCreate(&r->e0));
   HS_CUDA_TRY(cudaEventCreate(&r->e1));
   HS_CUDA_TRY(cudaEventRecord(r->e0, r->st));
-  int rc = p->ws_alloc(r->ws, r->N_G, p->N_f, r->st, true);
-  if (rc != HS_OK) return rc;
-  rc = p->enqueue(r->A, r->B, r->ld, r->U, r->N_G, r->H, r->S, r->ws, r->st, false);
-  if (rc != HS_OK) return rc;
+  return HS_OK;
+}
+
+int finish_launch(Request* r) {
   HS_CUDA_TRY(cudaEventRecord(r->e1, r->st));
   HS_CUDA_TRY(cudaLaunchHostFunc(r->st, on_done, r));
   return HS_OK;
 }
 
+// Launch one admitted request on its own stream (FP64 form).
+int launch(ServeState* S, Request* r) {
+  hs_plan_s* p = S->plan;
+  int rc = take_stream(S, r);
+  if (rc != HS_OK) return rc;
+  rc = p->ws_alloc(r->ws, r->N_G, p->N_f, r->st, true);
+  if (rc != HS_OK) return rc;
+  rc = p->enqueue(r->A, r->B, r->ld, r->U, r->N_G, r->H, r->S, r->ws, r->st, false);
+  if (rc != HS_OK) return rc;
+  return finish_launch(r);
+}
+
+// Split form: the requests admitted in one pass share one grouped per-atom launch.
+// Each request slices its inputs on its own stream; the batch stream waits for all
+// of them, replays the plan's graph (grouped MODE_ATOMS kernel over every request's
+// atoms), and each request stream waits for it before its own slicing of Z, Y, X,
+// its contractions and its mirror.  Returns per-request codes in rcs.
+void launch_batch(ServeState* S, std::vector<Request*>& batch, std::vector<int>& rcs) {
+  hs_plan_s* p = S->plan;
+  rcs.assign(batch.size(), HS_OK);
+  std::vector<AtomsJob> jobs;
+  std::vector<Request*> ready;
+  for (size_t i = 0; i < batch.size(); ++i) {
+    Request* r = batch[i];
+    int rc = take_stream(S, r);
+    if (rc == HS_OK) rc = p->ws_alloc(r->ws, r->N_G, p->N_f, r->st, true);
+    if (rc == HS_OK) rc = p->split_inputs(r->A, r->B, r->ld, r->U, r->N_G, r->ws, r->st);
+    if (rc == HS_OK && cudaEventCreateWithFlags(&r->e_in, cudaEventDisableTiming) != cudaSuccess)
+      rc = HS_ECUDA;
+    if (rc == HS_OK && cudaEventRecord(r->e_in, r->st) != cudaSuccess) rc = HS_ECUDA;
+    rcs[i] = rc;
+    if (rc == HS_OK) {
+      jobs.push_back(AtomsJob{&r->ws, r->N_G});
+      ready.push_back(r);
+    }
+  }
+  if (ready.empty()) return;
+  int rc = HS_OK;
+  cudaEvent_t e_atoms = nullptr;
+  if (!S->batch_stream &&
+      cudaStreamCreateWithFlags(&S->batch_stream, cudaStreamNonBlocking) != cudaSuccess)
+    rc = HS_ECUDA;
+  if (rc == HS_OK && !S->graph && !(S->graph = hs_atoms_graph_new())) rc = HS_ENOMEM;
+  for (Request* r : ready)
+    if (rc == HS_OK && cudaStreamWaitEvent(S->batch_stream, r->e_in, 0) != cudaSuccess)
+      rc = HS_ECUDA;
+  if (rc == HS_OK) rc = p->split_atoms(jobs.data(), (int)jobs.size(), S->batch_stream, S->graph);
+  if (rc == HS_OK && cudaEventCreateWithFlags(&e_atoms, cudaEventDisableTiming) != cudaSuccess)
+    rc = HS_ECUDA;
+  if (rc == HS_OK && cudaEventRecord(e_atoms, S->batch_stream) != cudaSuccess) rc = HS_ECUDA;
+  if (rc == HS_OK) {
+    S->batches += 1;
+    S->batched_requests += ready.size();
+  }
+  for (size_t i = 0, k = 0; i < batch.size(); ++i) {
+    if (rcs[i] != HS_OK) continue;
+    Request* r = ready[k++];
+    int rr = rc;
+    if (rr == HS_OK && cudaStreamWaitEvent(r->st, e_atoms, 0) != cudaSuccess) rr = HS_ECUDA;
+    if (rr == HS_OK) rr = p->split_outputs(r->A, r->ld, r->N_G, r->H, r->S, r->ws, r->st, false);
+    if (rr == HS_OK && hs_launch_mirror(r->S, r->N_G, r->N_G, r->st) != cudaSuccess) rr = HS_ECUDA;
+    if (rr == HS_OK && hs_launch_mirror(r->H, r->N_G, r->N_G, r->st) != cudaSuccess) rr = HS_ECUDA;
+    if (rr == HS_OK) rr = finish_launch(r);
+    rcs[i] = rr;
+  }
+  if (e_atoms) cudaEventDestroy(e_atoms);  // released once its waits are satisfied
+}
+
 void finish(ServeState* S, Request* r) {
   hs_plan_s* p = S->plan;
+  if (r->e_in) {
+    cudaEventDestroy(r->e_in);
+    r->e_in = nullptr;
+  }
   if (r->ws.Z || r->ws.W2) p->ws_free(r->ws, r->st);
   if (r->st) S->free_streams.push_back(r->st);
   S->in_use -= r->fp;
@@ -125,7 +200,9 @@ void scheduler(ServeState* S) {
       }
     }
     // admit in arrival order: the head blocks until it fits (FIFO fairness)
-    while (!S->queue.empty() && (int)S->running.size() < ServeState::kMaxRunning) {
+    std::vector<Request*> batch;
+    while (!S->queue.empty() && (int)(S->running.size() + batch.size()) < ServeState::kMaxRunning &&
+           (int)batch.size() < kAtomsBatchMax) {
       Request* r = S->queue.front();
       if (S->plan->budget && S->in_use + r->fp > S->plan->budget) break;
       S->queue.pop_front();
@@ -133,14 +210,25 @@ void scheduler(ServeState* S) {
       r->inflight_at_admit = S->in_use;
       r->t_admit = now_s();
       r->state = 1;
-      int rc = launch(S, r);
-      if (rc != HS_OK) {
-        cudaGetLastError();
-        r->rc = rc;
-        if (r->st) cudaStreamSynchronize(r->st);
-        finish(S, r);
+      batch.push_back(r);
+    }
+    if (!batch.empty()) {
+      std::vector<int> rcs(batch.size(), HS_OK);
+      if (S->plan->precision == HS_SPLIT_BF16) {
+        launch_batch(S, batch, rcs);
       } else {
-        S->running.push_back(r);
+        for (size_t i = 0; i < batch.size(); ++i) rcs[i] = launch(S, batch[i]);
+      }
+      for (size_t i = 0; i < batch.size(); ++i) {
+        Request* r = batch[i];
+        if (rcs[i] != HS_OK) {
+          cudaGetLastError();
+          r->rc = rcs[i];
+          if (r->st) cudaStreamSynchronize(r->st);
+          finish(S, r);
+        } else {
+          S->running.push_back(r);
+        }
       }
     }
     S->cv.notify_all();
@@ -205,6 +293,11 @@ void hs_plan_s::serve_shutdown() {
     if (r->e1) cudaEventDestroy(r->e1);
     delete r;
   }
+  if (S->batch_stream) {
+    cudaStreamSynchronize(S->batch_stream);
+    cudaStreamDestroy(S->batch_stream);
+  }
+  hs_atoms_graph_free(S->graph);
   for (cudaStream_t st : S->free_streams) cudaStreamDestroy(st);
   if (S->pool) cudaMemPoolDestroy(S->pool);
   delete S;
