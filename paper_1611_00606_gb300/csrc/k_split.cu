@@ -30,7 +30,13 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "plan.h"
@@ -1049,13 +1055,98 @@ static int graph_launch_atoms(AtomsGraph& G, int s, int grid, size_t smem, cudaS
   return HS_OK;
 }
 
+// ---------------------------------------------------------------- autotuner
+// Pipeline depth (TMA ring stages) of each kernel mode, tuned per (mode, slices,
+// N_L, N_G bucket of 1024): the first synchronous assembly with an untuned key
+// times every candidate depth on its real work (the trial launches compute the
+// same result as the final one) and keeps the fastest.  Serving requests use the
+// tuned value when there is one and the deepest ring otherwise.  HS_AUTOTUNE=0
+// disables tuning; HS_TUNE_CACHE=<file> loads and appends "key depth" lines.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(int mode, int s, int N_L, int N_G) {
+  return std::to_string(mode) + ":" + std::to_string(s) + ":" + std::to_string(N_L) + ":" +
+         std::to_string((N_G + 1023) / 1024);
+}
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("HS_TUNE_CACHE");
+  if (!path) return;
+  std::FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char key[128];
+  int v;
+  while (std::fscanf(f, "%127s %d", key, &v) == 2) g_tune[key] = v;
+  std::fclose(f);
+}
+
+void tune_store_locked(const std::string& key, int v) {
+  g_tune[key] = v;
+  const char* path = std::getenv("HS_TUNE_CACHE");
+  if (!path) return;
+  std::FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d\n", key.c_str(), v);
+  std::fclose(f);
+}
+
+size_t smem_for(int n_stage, int stage_bytes) {
+  return std::max((size_t)n_stage * stage_bytes, (size_t)STAGING_BYTES) + 1024 + 256;
+}
+
+// Depth for this launch; `trial(depth)` enqueues the real work with that depth.
+int tuned_depth(int mode, int s, int N_L, int N_G, int max_depth, bool allow, cudaStream_t st,
+                const std::function<int(int)>& trial) {
+  const std::string key = tune_key(mode, s, N_L, N_G);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return std::min(std::max(it->second, 2), max_depth);
+  }
+  const char* env = std::getenv("HS_AUTOTUNE");
+  if (!allow || (env && env[0] == '0')) return max_depth;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return max_depth;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return max_depth;
+  }
+  int best = max_depth;
+  float best_ms = 1e30f;
+  for (int d = max_depth; d >= 2; --d) {
+    float ms = 0.f;
+    if (cudaEventRecord(e0, st) != cudaSuccess || trial(d) != HS_OK ||
+        cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaGetLastError();
+      break;
+    }
+    if (ms < 0.98f * best_ms) {  // a shallower ring must win clearly
+      best_ms = ms;
+      best = d;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_store_locked(key, best);
+  return best;
+}
+}  // namespace
+
 int hs_plan_s::split_geometry(int& n_stage, size_t& smem) const {
   const int stage_bytes = 4 * slices * TILE_BYTES;
   const int budget = 227 * 1024 - 1024 - 256;
   n_stage = budget / stage_bytes;
   if (n_stage > 8) n_stage = 8;
   if (n_stage < 2) return HS_EINVAL;
-  smem = std::max((size_t)n_stage * stage_bytes, (size_t)STAGING_BYTES) + 1024 + 256;
+  smem = smem_for(n_stage, stage_bytes);
   return HS_OK;
 }
 
@@ -1140,8 +1231,16 @@ int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGr
   at.n_pad = np;
   at.ntile = np / BN;
   PA->s = s;
-  PA->n_stage = n_stage;
   PA->err = err_d;
+  const int stage_bytes = 4 * s * TILE_BYTES;
+  const int depth = tuned_depth(MODE_ATOMS, s, N_L, jobs[0].N_G, n_stage, graph == nullptr, st,
+                                [&](int d) {
+                                  PA->n_stage = d;
+                                  return launch_gemm(MODE_ATOMS, s, grid, smem_for(d, stage_bytes),
+                                                     st, *PA);
+                                });
+  PA->n_stage = depth;
+  smem = smem_for(depth, stage_bytes);
   rc = graph ? graph_launch_atoms(*graph, s, grid, smem, st, *PA)
              : launch_gemm(MODE_ATOMS, s, grid, smem, st, *PA);
   delete PA;
@@ -1225,6 +1324,15 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   P.seg[0] = seg(SRC_A, SRC_A, N_A);
   P.seg[1] = seg(SRC_UB, SRC_UB, N_A);
   P.C = S;
+  {
+    const int stage_bytes = 4 * s * TILE_BYTES;
+    const int depth = tuned_depth(MODE_CONTRACT, s, N_L, N_G, n_stage, timed, st, [&](int d) {
+      P.n_stage = d;
+      return launch_gemm(MODE_CONTRACT, s, tiles, smem_for(d, stage_bytes), st, P);
+    });
+    P.n_stage = depth;
+    smem = smem_for(depth, stage_bytes);
+  }
   rc = launch_gemm(MODE_CONTRACT, s, tiles, smem, st, P);
   if (rc == HS_OK && timed && cudaEventRecord(ev[6], st) != cudaSuccess) rc = HS_ECUDA;
   if (rc == HS_OK) {

@@ -162,3 +162,21 @@ def test_split_large_12000_panels(hs):
     assert eh <= TOL_SPLIT and es <= TOL_SPLIT
     assert list(np.nonzero(flags)[0]) == list(w.indefinite)
     assert np.array_equal(H[:, cols].conj().T[:, cols], H[np.ix_(cols, cols)])
+
+
+def test_autotuner_tunes_once_and_caches(hs, tmp_path, monkeypatch):
+    """The first assembly of a new (mode, slices, N_L, N_G bucket) key times every
+    pipeline depth and records the fastest; later calls reuse it, bit for bit."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("HS_TUNE_CACHE", str(path))
+    d = synth.make_inputs(synth.Workload("t", 3, 7, 700, (1,), seed=41))  # fresh N_L = 7 keys
+    H1, S1, _, _ = _run(hs, d, 3, 7)
+    words = path.read_text().split()
+    keys, depths = words[0::2], [int(v) for v in words[1::2]]
+    assert sorted(k.split(":")[0] for k in keys) == ["0", "1"]  # contraction and per-atom
+    assert all(2 <= v <= 8 for v in depths)
+    H2, S2, _, _ = _run(hs, d, 3, 7)
+    assert np.array_equal(H1, H2) and np.array_equal(S1, S2)
+    assert len(path.read_text().split()) == len(words)  # nothing re-tuned
+    Hr, Sr = assemble(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], 3, 7)
+    assert rel_frobenius(H1, Hr) <= TOL_SPLIT and rel_frobenius(S1, Sr) <= TOL_SPLIT
