@@ -10,12 +10,13 @@
 //                                                  d_p in [-256, 256] (p > 1)
 // with E_g chosen per column from the column's largest component (so that
 // max|x|/2^E_g lies in [64, 128)).  Every d_p * 2^{-9(p-1)} is exact in
-// BF16.  Products of two slices are exact; summed over a window of 256 real K
-// of 128 real K the slice-pair levels 0 (d_1 e_1), 1 (d_1 e_2 + d_2 e_1) and
+// BF16.  Products of two slices are exact; summed over a window of 128 real K
+// the slice-pair levels 0 (d_1 e_1), 1 (d_1 e_2 + d_2 e_1) and
 // 2 (d_1 e_3 + d_2 e_2 + d_3 e_1) stay within 2^24 units and are therefore
 // exact in FP32 tensor-core accumulators, whatever the accumulator's rounding.
-// Levels >= 3 (2^-27 and below) share a fourth, inexact accumulator.  After
-// every window the four TMEM accumulators are drained into a double-float
+// Levels >= 3 (2^-27 and below) share a fourth, inexact accumulator.  Level 0
+// stays exact for 1024 K and level 1 for 256 K, so those two are read out only
+// every 8th and every 2nd window.  Read-outs go into a double-float
 // (hi, lo FP32 pair) accumulator per output element, scaled by 2^{E_i + E_j}:
 // levels 0, 1 and 2 through an error-free TwoSum into hi, levels >= 3 into lo
 // (the leading digit is typically small, so level 2 is only ~2^-14 below
@@ -181,26 +182,45 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 }
 
 
-// Drain 16 TMEM columns of the four window accumulators (level k at column
-// offset k*BN) into (hi, lo) pairs kept in units of the current segment's
-// scale 2^(E_row + E_col): the window sums are exact integers (levels 0-2), so
-// levels 0, 1, 2 go through an error-free TwoSum into hi and levels >= 3 into lo.
-__device__ __forceinline__ void drain16(uint32_t taddr, int s, float (&hi)[16], float (&lo)[16]) {
+// Drain 16 TMEM columns of the accumulators in `mask` (level k at column offset
+// k*BN) into (hi, lo) pairs kept in units of the current segment's scale
+// 2^(E_row + E_col): the window sums of levels 0-2 are exact integers and go
+// through an error-free TwoSum into hi; levels >= 3 go into lo.
+template <int S, uint32_t MASK>
+__device__ __forceinline__ void drain16(uint32_t taddr, float (&hi)[16], float (&lo)[16]) {
+  constexpr bool r0 = MASK & 1u, r1 = MASK & 2u, r2 = S >= 3 && (MASK & 4u),
+                 r3 = S >= 4 && (MASK & 8u);
 #pragma unroll
   for (int c0 = 0; c0 < 16; c0 += 4) {
     float v0[4], v1[4], v2[4], v3[4];
-    tmem_ld4(taddr + c0, v0);
-    tmem_ld4(taddr + BN + c0, v1);
-    if (s >= 3) tmem_ld4(taddr + 2 * BN + c0, v2);
-    if (s >= 4) tmem_ld4(taddr + 3 * BN + c0, v3);
+    if (r0) tmem_ld4(taddr + c0, v0);
+    if (r1) tmem_ld4(taddr + BN + c0, v1);
+    if (r2) tmem_ld4(taddr + 2 * BN + c0, v2);
+    if (r3) tmem_ld4(taddr + 3 * BN + c0, v3);
     tmem_wait_ld();
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      two_sum_acc(hi[c0 + c], lo[c0 + c], v0[c]);
-      two_sum_acc(hi[c0 + c], lo[c0 + c], v1[c]);
-      if (s >= 3) two_sum_acc(hi[c0 + c], lo[c0 + c], v2[c]);
-      if (s >= 4) lo[c0 + c] += v3[c];
+      if (r0) two_sum_acc(hi[c0 + c], lo[c0 + c], v0[c]);
+      if (r1) two_sum_acc(hi[c0 + c], lo[c0 + c], v1[c]);
+      if (r2) two_sum_acc(hi[c0 + c], lo[c0 + c], v2[c]);
+      if (r3) lo[c0 + c] += v3[c];
     }
+  }
+}
+
+// Both 64-column strips of one window read-out; `mask` is one of due_mask()'s values.
+template <int S>
+__device__ __forceinline__ void drain_window(uint32_t tl, uint32_t mask, float (&h0)[16],
+                                             float (&l0)[16], float (&h1)[16], float (&l1)[16]) {
+  if (mask == 0xFu) {
+    drain16<S, 0xFu>(tl, h0, l0);
+    drain16<S, 0xFu>(tl + (uint32_t)BNC, h1, l1);
+  } else if (mask == 0xEu) {
+    drain16<S, 0xEu>(tl, h0, l0);
+    drain16<S, 0xEu>(tl + (uint32_t)BNC, h1, l1);
+  } else {
+    drain16<S, 0xCu>(tl, h0, l0);
+    drain16<S, 0xCu>(tl + (uint32_t)BNC, h1, l1);
   }
 }
 
@@ -369,10 +389,24 @@ __device__ __forceinline__ SegInfo seg_info(const SplitParams& P, const TileId& 
 // accumulator of level min(p + q, 3).  Fully unrolled for a compile-time slice
 // count; the descriptors of slice p / q are the stage's base descriptors plus a
 // constant (the 14-bit start-address field holds address >> 4 and stays below
-// 2^14 for any smem address).  `first` = first stage of a window: the first
-// pair of every level overwrites its accumulator instead of adding to it.
+// 2^14 for any smem address).  Accumulators in `init_mask` restart: the first
+// pair of their level overwrites instead of adding.
+// Accumulators read out after window w of a segment (bit k: accumulator k).  Each
+// level stays exact for as long as its bound allows: level 0 (<= 2^14 per real K)
+// for 1024 K = 8 windows, level 1 (<= 2^16) for 256 K = 2 windows, level 2 for one
+// window; levels >= 3 are inexact and read every window.  The last window of a
+// segment reads everything (the next segment has another scale).
+__device__ __forceinline__ uint32_t due_mask(int w, bool last) {
+  if (last) return 0xFu;
+  uint32_t m = 0xCu;                 // levels 2 and >= 3
+  if ((w & 1) == 1) m |= 0x2u;       // level 1
+  if ((w & 7) == 7) m |= 0x1u;       // level 0
+  return m;
+}
+
 template <int S>
-__device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t ad0, uint64_t bd0, bool first) {
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t ad0, uint64_t bd0,
+                                            uint32_t init_mask) {
 #pragma unroll
   for (int p = 0; p < S; ++p) {
 #pragma unroll
@@ -382,7 +416,7 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t ad0, uint64_
       const int acc = lvl < 3 ? lvl : 3;
       const bool lead = (p == 0 && q == acc);  // first pair of its level within a stage
       tc_mma_bf16(tmem + acc * BN, ad0 + (uint64_t)(p * kStep), bd0 + (uint64_t)(q * kStep), kIdesc,
-                  (lead && first) ? 0u : 1u);
+                  (lead && ((init_mask >> acc) & 1u)) ? 0u : 1u);
     }
   }
 }
@@ -493,6 +527,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
       bool ok = true;
       for (int sg = 0; sg < T.nseg && ok; ++sg) {
         const int kbn = seg_info<MODE>(P, T, sg).kblocks;
+        uint32_t restart = 0xFu;  // accumulators to restart in the next window
         for (int w0 = 0; w0 < kbn && ok; w0 += WIN) {
           if (nwin > 0 && !mbar_wait(acc_empty, (uint32_t)(nwin - 1) & 1u, abort_flag)) {
             ok = false;
@@ -500,6 +535,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           }
           tc_fence_after();
           const int w1 = min(kbn, w0 + WIN);
+          const uint32_t first_mask = restart;
+          restart = due_mask(w0 / WIN, w1 == kbn);
           for (int kb = w0; kb < w1; ++kb) {
             if (!mbar_wait(&full[slot], phase, abort_flag)) {
               ok = false;
@@ -507,7 +544,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
             }
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + slot * stage_bytes);
-            issue_stage<S>(tmem, sdesc_sw32(sa), sdesc_sw32(sa + a_bytes), kb == w0);
+            issue_stage<S>(tmem, sdesc_sw32(sa), sdesc_sw32(sa + a_bytes),
+                           kb == w0 ? first_mask : 0u);
             tc_commit(&empty[slot]);
             if (++slot == NS) {
               slot = 0;
@@ -565,8 +603,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           break;
         }
         tc_fence_after();
-        drain16(tl, s, h0, l0);
-        drain16(tl + (uint32_t)BNC, s, h1, l1);
+        drain_window<S>(tl, due_mask(w0 / WIN, w0 + WIN >= si.kblocks), h0, l0, h1, l1);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acc_empty);
