@@ -173,11 +173,41 @@ __device__ __forceinline__ float pow2f(int e) {
   e = e < -126 ? -126 : (e > 127 ? 127 : e);
   return __int_as_float((e + 127) << 23);
 }
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
-  const float s = hi + v;
-  const float bp = s - hi;
-  const float ap = s - bp;
-  lo += (hi - ap) + (v - bp);
+// Column pairs of the (hi, lo) accumulators live in 64-bit registers and are
+// updated with Blackwell's packed FP32 pair arithmetic (round to nearest, as
+// TwoSum requires), two columns per instruction.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pack2(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(f32x2 r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+// Error-free TwoSum of both lanes: hi + v = s + e exactly; hi = s, lo += e.
+__device__ __forceinline__ void two_sum_acc2(f32x2& hi, f32x2& lo, f32x2 v) {
+  const f32x2 s = add2(hi, v);
+  const f32x2 bp = sub2(s, hi);
+  const f32x2 ap = sub2(s, bp);
+  lo = add2(lo, add2(sub2(hi, ap), sub2(v, bp)));
   hi = s;
 }
 
@@ -187,7 +217,7 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 // 2^(E_row + E_col): the window sums of levels 0-2 are exact integers and go
 // through an error-free TwoSum into hi; levels >= 3 go into lo.
 template <int S, uint32_t MASK>
-__device__ __forceinline__ void drain16(uint32_t taddr, float (&hi)[16], float (&lo)[16]) {
+__device__ __forceinline__ void drain16(uint32_t taddr, f32x2 (&hi)[8], f32x2 (&lo)[8]) {
   constexpr bool r0 = MASK & 1u, r1 = MASK & 2u, r2 = S >= 3 && (MASK & 4u),
                  r3 = S >= 4 && (MASK & 8u);
 #pragma unroll
@@ -199,19 +229,20 @@ __device__ __forceinline__ void drain16(uint32_t taddr, float (&hi)[16], float (
     if (r3) tmem_ld4(taddr + 3 * BN + c0, v3);
     tmem_wait_ld();
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      if (r0) two_sum_acc(hi[c0 + c], lo[c0 + c], v0[c]);
-      if (r1) two_sum_acc(hi[c0 + c], lo[c0 + c], v1[c]);
-      if (r2) two_sum_acc(hi[c0 + c], lo[c0 + c], v2[c]);
-      if (r3) lo[c0 + c] += v3[c];
+    for (int c = 0; c < 4; c += 2) {
+      const int k = (c0 + c) >> 1;
+      if (r0) two_sum_acc2(hi[k], lo[k], pack2(v0[c], v0[c + 1]));
+      if (r1) two_sum_acc2(hi[k], lo[k], pack2(v1[c], v1[c + 1]));
+      if (r2) two_sum_acc2(hi[k], lo[k], pack2(v2[c], v2[c + 1]));
+      if (r3) lo[k] = add2(lo[k], pack2(v3[c], v3[c + 1]));
     }
   }
 }
 
 // Both 64-column strips of one window read-out; `mask` is one of due_mask()'s values.
 template <int S>
-__device__ __forceinline__ void drain_window(uint32_t tl, uint32_t mask, float (&h0)[16],
-                                             float (&l0)[16], float (&h1)[16], float (&l1)[16]) {
+__device__ __forceinline__ void drain_window(uint32_t tl, uint32_t mask, f32x2 (&h0)[8],
+                                             f32x2 (&l0)[8], f32x2 (&h1)[8], f32x2 (&l1)[8]) {
   if (mask == 0xFu) {
     drain16<S, 0xFu>(tl, h0, l0);
     drain16<S, 0xFu>(tl + (uint32_t)BNC, h1, l1);
@@ -276,7 +307,7 @@ struct AtomsArgs {
   int n_pad, ntile;
 };
 
-struct __align__(64) SplitParams {
+struct SplitParams {
   CUtensorMap maps[kMaxMaps];
   SplitSeg seg[kMaxSeg];
   int nseg;
@@ -572,9 +603,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
     const int cg = (warp - 2) >> 2;  // 16-column group of each 64-column strip
     const int row = T.i0 + 32 * q4 + lane;
     const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(16 * cg);
-    float h0[16], l0[16], h1[16], l1[16];  // strip 0 (TMEM cols < 64), strip 1
+    f32x2 h0[8], l0[8], h1[8], l1[8];  // column pairs of strip 0 (TMEM cols < 64), strip 1
 #pragma unroll
-    for (int c = 0; c < 16; ++c) h0[c] = l0[c] = h1[c] = l1[c] = 0.f;
+    for (int c = 0; c < 8; ++c) h0[c] = l0[c] = h1[c] = l1[c] = 0ull;
     int nwin = 0;
     bool ok = true;
     int eRow = 0, eC0 = 0, eC1 = 0;  // current segment's exponents (lane c: column c)
@@ -585,13 +616,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
       const int nC1 = si.eC1[16 * cg + (lane & 15)];
       if (sg > 0) {  // move the pairs into the new segment's units (exact powers of two)
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float f0 = pow2f(eRow - nRow + __shfl_sync(0xffffffffu, eC0 - nC0, c));
-          const float f1 = pow2f(eRow - nRow + __shfl_sync(0xffffffffu, eC1 - nC1, c));
-          h0[c] *= f0;
-          l0[c] *= f0;
-          h1[c] *= f1;
-          l1[c] *= f1;
+        for (int c = 0; c < 16; c += 2) {
+          const int dr = eRow - nRow;
+          const f32x2 f0 = pack2(pow2f(dr + __shfl_sync(0xffffffffu, eC0 - nC0, c)),
+                                 pow2f(dr + __shfl_sync(0xffffffffu, eC0 - nC0, c + 1)));
+          const f32x2 f1 = pack2(pow2f(dr + __shfl_sync(0xffffffffu, eC1 - nC1, c)),
+                                 pow2f(dr + __shfl_sync(0xffffffffu, eC1 - nC1, c + 1)));
+          h0[c >> 1] = mul2(h0[c >> 1], f0);
+          l0[c >> 1] = mul2(l0[c >> 1], f0);
+          h1[c >> 1] = mul2(h1[c >> 1], f1);
+          l1[c >> 1] = mul2(l1[c >> 1], f1);
         }
       }
       eRow = nRow;
@@ -623,9 +657,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
     int* s_ecol = s_erow + 128;                        // [2][64]
     const int r = 32 * q4 + lane;
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      stg[(0 * 64 + 16 * cg + c) * 128 + r] = make_float2(h0[c], l0[c]);
-      stg[(1 * 64 + 16 * cg + c) * 128 + r] = make_float2(h1[c], l1[c]);
+    for (int c = 0; c < 16; c += 2) {
+      const float2 ha = unpack2(h0[c >> 1]), la = unpack2(l0[c >> 1]);
+      const float2 hb = unpack2(h1[c >> 1]), lb = unpack2(l1[c >> 1]);
+      stg[(0 * 64 + 16 * cg + c) * 128 + r] = make_float2(ha.x, la.x);
+      stg[(0 * 64 + 16 * cg + c + 1) * 128 + r] = make_float2(ha.y, la.y);
+      stg[(1 * 64 + 16 * cg + c) * 128 + r] = make_float2(hb.x, lb.x);
+      stg[(1 * 64 + 16 * cg + c + 1) * 128 + r] = make_float2(hb.y, lb.y);
     }
     if (cg == 0) s_erow[r] = eRow;
     if (q4 == 0 && lane < 16) {
