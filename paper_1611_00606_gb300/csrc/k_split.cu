@@ -118,6 +118,28 @@ __device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* m
       "l"((uint64_t)map), "r"(0), "r"(0), "r"(kb), "r"(rb), "r"(plane), "r"(smem_u32(bar))
       : "memory");
 }
+// The same box, written at this smem offset into every CTA of the cluster in
+// `mask`, each CTA's mbarrier at `bar`'s offset receiving the byte count.
+__device__ __forceinline__ void tma_load_tile_mc(uint32_t dst, const CUtensorMap* map, int kb,
+                                                 int rb, int plane, uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%2, %3, %4, %5, %6}], [%7], %8;" ::"r"(dst),
+      "l"((uint64_t)map), "r"(0), "r"(0), "r"(kb), "r"(rb), "r"(plane), "r"(smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Every thread of every CTA of the cluster.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
 }
@@ -131,6 +153,15 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
+      : "memory");
+}
+// Arrive on the mbarrier at `bar`'s offset in every CTA of `mask` once this
+// thread's MMAs issued so far have completed.
+__device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
       : "memory");
 }
 __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
@@ -346,15 +377,19 @@ template <int MODE>
 __device__ __forceinline__ TileId decode_tile(const SplitParams& P) {
   TileId t{};
   if (MODE == MODE_CONTRACT) {
-    int b = blockIdx.x, bi = 0;
+    // clusters of two CTAs: column blocks 2m and 2m + 1 of one row block (which
+    // share the L' tiles); row block bi holds min(2 bi + 2, nbj) column blocks, so
+    // only an odd nbj leaves the last pair a block past the matrix (zero slices,
+    // nothing stored)
+    int b = blockIdx.x >> 1, bi = 0;
     for (;;) {
-      const int n = min(2 * bi + 2, P.nbj);
+      const int n = (min(2 * bi + 2, P.nbj) + 1) >> 1;
       if (b < n) break;
       b -= n;
       ++bi;
     }
     t.i0 = bi * BM;
-    t.j0 = b * BNC;
+    t.j0 = (2 * b + (int)cluster_rank()) * BNC;
     t.nseg = P.nseg;
     t.N_G = P.N_G;
   } else {
@@ -458,6 +493,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int s = S;
+  // CTAs per cluster: a contraction pairs two tiles of one row block, each CTA
+  // loading half of the shared L' boxes for both (TMA multicast)
+  constexpr int CL = MODE == MODE_CONTRACT ? 2 : 1;
   const int NS = P.n_stage;
   const uint32_t a_bytes = (uint32_t)s * 2 * TILE_BYTES;   // s slices x 128 rows
   const uint32_t stage_bytes = 2 * a_bytes;                 // A part + B part
@@ -475,7 +513,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   if (threadIdx.x == 0) {
     for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
+      mbar_init(&empty[i], CL);  // released by the MMA thread of every CTA
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, NUM_DRAIN_WARPS);
@@ -499,6 +537,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   }
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) cluster_sync();  // the peer's barriers are initialised before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -524,9 +563,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           const uint32_t sb = sa + a_bytes;
           const int kl = si.kbL + kb, kr = si.kbR + kb;
           for (int p = 0; p < s; ++p) {
-            tma_load_tile(sa + p * 2 * TILE_BYTES, si.mL, kl, si.rbL, si.plL + p, &full[slot]);
-            tma_load_tile(sa + p * 2 * TILE_BYTES + TILE_BYTES, si.mL, kl, si.rbL + 1, si.plL + p,
-                          &full[slot]);
+            if (CL == 1) {
+              tma_load_tile(sa + p * 2 * TILE_BYTES, si.mL, kl, si.rbL, si.plL + p, &full[slot]);
+              tma_load_tile(sa + p * 2 * TILE_BYTES + TILE_BYTES, si.mL, kl, si.rbL + 1,
+                            si.plL + p, &full[slot]);
+            } else {  // this CTA's 64-row half of the L' box, into both CTAs
+              const int h = (int)cluster_rank();
+              tma_load_tile_mc(sa + p * 2 * TILE_BYTES + h * TILE_BYTES, si.mL, kl, si.rbL + h,
+                               si.plL + p, &full[slot], (uint16_t)0x3);
+            }
             tma_load_tile(sb + p * 2 * TILE_BYTES, si.mR1, kr, si.rbR1, si.plR + p, &full[slot]);
             tma_load_tile(sb + p * 2 * TILE_BYTES + TILE_BYTES, si.mR2, kr, si.rbR2, si.plR + p,
                           &full[slot]);
@@ -548,6 +593,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           while (!mbar_try(&full[i], (armed_par >> i) & 1u))
             if (globaltimer() - t0 > kWaitNs) break;
         }
+      // nor with the peer's releases of this CTA's stages still to arrive
+      if (CL > 1 && ok && !*abort_flag)
+        for (int i = 0; i < NS; ++i)
+          if (armed & (1u << i)) {
+            uint64_t t0 = globaltimer();
+            while (!mbar_try(&empty[i], (armed_par >> i) & 1u))
+              if (globaltimer() - t0 > kWaitNs) break;
+          }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer (one thread)
@@ -577,7 +630,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
             const uint32_t sa = smem_u32(smem + slot * stage_bytes);
             issue_stage<S>(tmem, sdesc_sw32(sa), sdesc_sw32(sa + a_bytes),
                            kb == w0 ? first_mask : 0u);
-            tc_commit(&empty[slot]);
+            if (CL == 1) tc_commit(&empty[slot]);
+            else tc_commit_mc(&empty[slot], (uint16_t)0x3);
             if (++slot == NS) {
               slot = 0;
               phase ^= 1u;
@@ -708,6 +762,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
 
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) cluster_sync();  // no multicast or remote arrive targets an exited CTA
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
@@ -1052,8 +1107,25 @@ template <int MODE, int S>
 static int launch_one(int grid, size_t smem, cudaStream_t st, const SplitParams& P) {
   int rc = set_smem((const void*)k_split_gemm<MODE, S>, smem);
   if (rc) return rc;
-  k_split_gemm<MODE, S><<<grid, NUM_THREADS, smem, st>>>(P);
-  return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
+  if (MODE == MODE_ATOMS) {
+    k_split_gemm<MODE, S><<<grid, NUM_THREADS, smem, st>>>(P);
+    return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
+  }
+  // contraction: clusters of two CTAs (grid is even)
+  if (grid % 2 != 0) return HS_EINVAL;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(NUM_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_split_gemm<MODE, S>, P) == cudaSuccess ? HS_OK : HS_ECUDA;
 }
 
 template <int MODE>
@@ -1383,7 +1455,7 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   P.err = err_d;
   const int nbi = (N_G + BM - 1) / BM;
   int tiles = 0;
-  for (int b = 0; b < nbi; ++b) tiles += std::min(2 * b + 2, P.nbj);
+  for (int b = 0; b < nbi; ++b) tiles += 2 * ((std::min(2 * b + 2, P.nbj) + 1) / 2);  // CTA pairs
   auto seg = [&](int srcL, int srcR, int nblk) {
     SplitSeg g;
     g.mL = map_of[srcL][0];
