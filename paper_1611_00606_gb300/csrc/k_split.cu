@@ -345,6 +345,7 @@ struct SplitParams {
   int s;          // slices
   int n_stage;    // pipeline depth
   int N_G, ldC, nbj;
+  int nbi, band;   // contraction: 128-row blocks, row blocks per band of the tile order
   int rows_pad;   // slice p of a coefficient-side array starts at row p * rows_pad
   double2* C;
   int* err;
@@ -377,19 +378,33 @@ template <int MODE>
 __device__ __forceinline__ TileId decode_tile(const SplitParams& P) {
   TileId t{};
   if (MODE == MODE_CONTRACT) {
-    // clusters of two CTAs: column blocks 2m and 2m + 1 of one row block (which
-    // share the L' tiles); row block bi holds min(2 bi + 2, nbj) column blocks, so
+    // Clusters of two CTAs: column blocks 2c and 2c + 1 of one row block (which
+    // share the L' tiles); row block bi holds column pairs c <= bi (c < npr), so
     // only an odd nbj leaves the last pair a block past the matrix (zero slices,
-    // nothing stored)
-    int b = blockIdx.x >> 1, bi = 0;
-    for (;;) {
-      const int n = (min(2 * bi + 2, P.nbj) + 1) >> 1;
-      if (b < n) break;
-      b -= n;
-      ++bi;
+    // nothing stored).  Pairs are numbered band by band (P.band row blocks per
+    // band) and column-major inside a band, so the CTAs resident at one time
+    // cover a compact block of rows x columns and share their operand tiles in L2.
+    const int npr = (P.nbj + 1) >> 1;
+    int p = blockIdx.x >> 1, bi = 0, c = 0;
+    for (int b0 = 0; b0 < P.nbi; b0 += P.band) {
+      const int b1 = min(b0 + P.band, P.nbi);
+      int n = 0;
+      for (int r = b0; r < b1; ++r) n += min(r + 1, npr);
+      if (p < n) {
+        for (c = 0; c < npr; ++c) {
+          const int lo = max(b0, c), cnt = b1 - lo;
+          if (p < cnt) {
+            bi = lo + p;
+            break;
+          }
+          p -= cnt;
+        }
+        break;
+      }
+      p -= n;
     }
     t.i0 = bi * BM;
-    t.j0 = (2 * b + (int)cluster_rank()) * BNC;
+    t.j0 = (2 * c + (int)cluster_rank()) * BNC;
     t.nseg = P.nseg;
     t.N_G = P.N_G;
   } else {
@@ -542,46 +557,54 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    // ---------------- TMA producer
-    if (lane == 0) {
-      int slot = 0;
-      uint32_t phase = 0;
-      uint32_t armed = 0;        // bit i: slot i was armed at least once
-      uint32_t armed_par = 0;    // bit i: parity of the last armed phase of slot i
-      bool ok = true;
-      for (int sg = 0; sg < T.nseg && ok; ++sg) {
-        const SegInfo si = seg_info<MODE>(P, T, sg);
-        for (int kb = 0; kb < si.kblocks; ++kb) {
-          if (!mbar_wait(&empty[slot], phase ^ 1u, abort_flag)) {
-            ok = false;
-            break;
-          }
-          mbar_expect_tx(&full[slot], stage_bytes);
-          armed |= 1u << slot;
-          armed_par = (armed_par & ~(1u << slot)) | (phase << slot);
-          const uint32_t sa = smem_u32(smem + slot * stage_bytes);
-          const uint32_t sb = sa + a_bytes;
-          const int kl = si.kbL + kb, kr = si.kbR + kb;
-          for (int p = 0; p < s; ++p) {
-            if (CL == 1) {
-              tma_load_tile(sa + p * 2 * TILE_BYTES, si.mL, kl, si.rbL, si.plL + p, &full[slot]);
-              tma_load_tile(sa + p * 2 * TILE_BYTES + TILE_BYTES, si.mL, kl, si.rbL + 1,
-                            si.plL + p, &full[slot]);
-            } else {  // this CTA's 64-row half of the L' box, into both CTAs
-              const int h = (int)cluster_rank();
-              tma_load_tile_mc(sa + p * 2 * TILE_BYTES + h * TILE_BYTES, si.mL, kl, si.rbL + h,
-                               si.plL + p, &full[slot], (uint16_t)0x3);
-            }
-            tma_load_tile(sb + p * 2 * TILE_BYTES, si.mR1, kr, si.rbR1, si.plR + p, &full[slot]);
-            tma_load_tile(sb + p * 2 * TILE_BYTES + TILE_BYTES, si.mR2, kr, si.rbR2, si.plR + p,
-                          &full[slot]);
-          }
-          if (++slot == NS) {
-            slot = 0;
-            phase ^= 1u;
+    // ---------------- TMA producer: lane 0 waits for free stages and arms them;
+    // the stage's boxes are then issued by one lane each, in one warp instruction
+    constexpr int NB = CL == 1 ? 4 : 3;  // boxes per slice: L' (two halves or ours), R', R''
+    int slot = 0;
+    uint32_t phase = 0;
+    uint32_t armed = 0;        // bit i: slot i was armed at least once
+    uint32_t armed_par = 0;    // bit i: parity of the last armed phase of slot i
+    bool ok = true;
+    const int bp = lane / NB, bk = lane - bp * NB;  // this lane's slice and box kind
+    const int h = (int)cluster_rank();
+    for (int sg = 0; sg < T.nseg && ok; ++sg) {
+      const SegInfo si = seg_info<MODE>(P, T, sg);
+      for (int kb = 0; kb < si.kblocks; ++kb) {
+        if (lane == 0) {
+          ok = mbar_wait(&empty[slot], phase ^ 1u, abort_flag);
+          if (ok) mbar_expect_tx(&full[slot], stage_bytes);
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        armed |= 1u << slot;
+        armed_par = (armed_par & ~(1u << slot)) | (phase << slot);
+        const uint32_t sa = smem_u32(smem + slot * stage_bytes);
+        const uint32_t sb = sa + a_bytes;
+        const int kl = si.kbL + kb, kr = si.kbR + kb;
+        if (bp < s) {
+          const uint32_t da = sa + bp * 2 * TILE_BYTES, db = sb + bp * 2 * TILE_BYTES;
+          if (CL == 1) {
+            if (bk == 0) tma_load_tile(da, si.mL, kl, si.rbL, si.plL + bp, &full[slot]);
+            else if (bk == 1)
+              tma_load_tile(da + TILE_BYTES, si.mL, kl, si.rbL + 1, si.plL + bp, &full[slot]);
+            else if (bk == 2) tma_load_tile(db, si.mR1, kr, si.rbR1, si.plR + bp, &full[slot]);
+            else tma_load_tile(db + TILE_BYTES, si.mR2, kr, si.rbR2, si.plR + bp, &full[slot]);
+          } else {  // bk 0: this CTA's 64-row half of the L' box, into both CTAs
+            if (bk == 0)
+              tma_load_tile_mc(da + h * TILE_BYTES, si.mL, kl, si.rbL + h, si.plL + bp, &full[slot],
+                               (uint16_t)0x3);
+            else if (bk == 1) tma_load_tile(db, si.mR1, kr, si.rbR1, si.plR + bp, &full[slot]);
+            else tma_load_tile(db + TILE_BYTES, si.mR2, kr, si.rbR2, si.plR + bp, &full[slot]);
           }
         }
+        __syncwarp();
+        if (++slot == NS) {
+          slot = 0;
+          phase ^= 1u;
+        }
       }
+    }
+    if (lane == 0) {
       if (!ok) {
         atomicExch(P.err, 1);
         *abort_flag = 1;
@@ -1287,6 +1310,17 @@ int tuned_depth(int mode, int s, int N_L, int N_G, int max_depth, bool allow, cu
 }
 }  // namespace
 
+// Row blocks per band of the contraction's tile order: 8 (76 resident clusters
+// then span about 8 row blocks x 19 column blocks); HS_BAND overrides.
+static int contract_band() {
+  static const int band = []() {
+    const char* e = std::getenv("HS_BAND");
+    const int v = e ? std::atoi(e) : 0;
+    return v >= 1 ? v : 8;
+  }();
+  return band;
+}
+
 int hs_plan_s::split_geometry(int& n_stage, size_t& smem) const {
   const int stage_bytes = 4 * slices * TILE_BYTES;
   const int budget = 227 * 1024 - 1024 - 256;
@@ -1455,7 +1489,9 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   P.err = err_d;
   const int nbi = (N_G + BM - 1) / BM;
   int tiles = 0;
-  for (int b = 0; b < nbi; ++b) tiles += 2 * ((std::min(2 * b + 2, P.nbj) + 1) / 2);  // CTA pairs
+  for (int b = 0; b < nbi; ++b) tiles += 2 * std::min(b + 1, (P.nbj + 1) / 2);  // CTA pairs
+  P.nbi = nbi;
+  P.band = contract_band();
   auto seg = [&](int srcL, int srcR, int nblk) {
     SplitSeg g;
     g.mL = map_of[srcL][0];
