@@ -18,9 +18,12 @@
 // stays exact for 1024 K and level 1 for 256 K, so those two are read out only
 // every 8th and every 2nd window.  Read-outs go into a double-float
 // (hi, lo FP32 pair) accumulator per output element, scaled by 2^{E_i + E_j}:
-// levels 0, 1 and 2 through an error-free TwoSum into hi, levels >= 3 into lo
-// (the leading digit is typically small, so level 2 is only ~2^-14 below
-// level 0 and would cap the pair's precision if it went to lo directly).
+// levels 0, 1 and 2 into hi with their rounding errors into lo, levels >= 3 into
+// lo (the leading digit is typically small, so level 2 is only ~2^-14 below
+// level 0 and would cap the pair's precision if it went to lo directly).  Levels
+// 0 and 1 take an error-free TwoSum; level 2, far below hi, takes Fast2Sum (half
+// the operations), error-free whenever |hi| >= |level-2 value|, and otherwise
+// (a running sum within ~2^-14 of zero) off by at most ~2^-24 of that value.
 // The pair is summed to FP64 once per tile at the end.
 //
 // Complex arithmetic on real tensor cores: with the K-major interleaved
@@ -243,10 +246,18 @@ __device__ __forceinline__ void two_sum_acc2(f32x2& hi, f32x2& lo, f32x2 v) {
 }
 
 
+// Fast2Sum of both lanes (exact when |hi| >= |v|): hi + v = s + e; hi = s, lo += e.
+__device__ __forceinline__ void fast_two_sum_acc2(f32x2& hi, f32x2& lo, f32x2 v) {
+  const f32x2 s = add2(hi, v);
+  lo = add2(lo, sub2(v, sub2(s, hi)));
+  hi = s;
+}
+
 // Drain 16 TMEM columns of the accumulators in `mask` (level k at column offset
 // k*BN) into (hi, lo) pairs kept in units of the current segment's scale
-// 2^(E_row + E_col): the window sums of levels 0-2 are exact integers and go
-// through an error-free TwoSum into hi; levels >= 3 go into lo.
+// 2^(E_row + E_col): the window sums of levels 0-2 are exact integers and go into
+// hi (TwoSum for levels 0 and 1, Fast2Sum for level 2, read after them); levels
+// >= 3 go into lo.
 template <int S, uint32_t MASK>
 __device__ __forceinline__ void drain16(uint32_t taddr, f32x2 (&hi)[8], f32x2 (&lo)[8]) {
   constexpr bool r0 = MASK & 1u, r1 = MASK & 2u, r2 = S >= 3 && (MASK & 4u),
@@ -264,7 +275,7 @@ __device__ __forceinline__ void drain16(uint32_t taddr, f32x2 (&hi)[8], f32x2 (&
       const int k = (c0 + c) >> 1;
       if (r0) two_sum_acc2(hi[k], lo[k], pack2(v0[c], v0[c + 1]));
       if (r1) two_sum_acc2(hi[k], lo[k], pack2(v1[c], v1[c + 1]));
-      if (r2) two_sum_acc2(hi[k], lo[k], pack2(v2[c], v2[c + 1]));
+      if (r2) fast_two_sum_acc2(hi[k], lo[k], pack2(v2[c], v2[c + 1]));
       if (r3) lo[k] = add2(lo[k], pack2(v3[c], v3[c + 1]));
     }
   }
