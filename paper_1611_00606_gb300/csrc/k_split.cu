@@ -345,7 +345,7 @@ struct AtomsArgs {
   const int* eOp[2];      // operator row exponents [a][n_pad]
   const int* slot;        // W2 slot of each atom
   int ld;
-  int N_A, N_L, P;        // P: padded real K of one atom block (multiple of KB)
+  int N_A, N_L, P;        // P: operator K per part (an atom's widest K block range)
   int n_pad, ntile;
 };
 
@@ -462,14 +462,14 @@ __device__ __forceinline__ SegInfo seg_info(const SplitParams& P, const TileId& 
     const AtomsReq& R = A.rq[t.r];
     si.mL = &P.maps[sg == 0 ? R.mA : R.mB];
     si.mR1 = si.mR2 = &P.maps[A.mOp[t.job]];
-    si.kbL = t.a * (A.P / KB);
+    si.kbL = (2 * t.a * A.N_L) / KB;  // atom a's rows in the packed layout
     si.rbL = t.i0 >> 6;
     si.plL = 0;
     si.kbR = sg * (A.P / KB);  // Z operator: A part in [0, P), B part in [P, 2P)
     si.rbR1 = t.n0 >> 6;
     si.rbR2 = (t.n0 >> 6) + 1;
     si.plR = t.a * P.s;
-    si.kblocks = A.P / KB;
+    si.kblocks = (2 * (t.a + 1) * A.N_L + KB - 1) / KB - si.kbL;
     si.eRow = sg == 0 ? R.eA : R.eB;
     si.eC0 = A.eOp[t.job] + t.a * A.n_pad + t.n0;
     si.eC1 = si.eC0 + 64;
@@ -805,10 +805,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
 
 // ------------------------------------------------------------------ slicers
 
-// Layout shared by every slice array.  Along K: complex row k of a source with
-// blocks of N_L rows (atoms or slots) sits at real position
-// (k / N_L) * P + 2 (k % N_L) (+1 for the imaginary part), P = roundup(2 N_L, 16),
-// the gaps holding zeros, so every atom block starts on a 16-element boundary.
+// Layout shared by every coefficient-side slice array.  Along K the source's
+// complex rows are packed: row k sits at real position 2k (+1 for the imaginary
+// part), and the length 2 nblk N_L is padded with zeros to kpad = roundup(., 16).
+// A contraction runs over kpad real K; the per-atom products read atom a's rows
+// [2 a N_L, 2 (a+1) N_L) as whole 16-wide K blocks, the operator slices of atom a
+// being shifted by the same offset (2 a N_L) mod 16 and zero outside the atom.
 // In memory each slice plane is blocked as [64-row block][16-wide K block][64 rows]
 // [16 elements]: one 2 KB tile per (row block, K block), contiguous, which is
 // exactly one TMA box (the TMA applies the 32-byte swizzle on the way to smem).
@@ -819,14 +821,14 @@ __device__ __forceinline__ size_t tile_off(int row, int j, int NKB) {
 struct SliceJob {
   const double2* X;  // source: nblk * N_L complex rows x N_G, column-major, ld ldX
   const double* u;   // optional real row weight (the U norms), may be null
-  uint16_t* plain;   // [s][rows_pad][nblk * P] BF16 slices of (re, im) pairs
+  uint16_t* plain;   // [s][rows_pad][kpad] BF16 slices of (re, im) pairs
   uint16_t* rot;     // same for (im, -re) pairs, may be null
   int* expo;         // [rows_pad] column exponents
   int ldX, nblk;
 };
 struct SliceParams {
   SliceJob job[kMaxJobs];
-  int s, N_G, rows_pad, N_L, P;
+  int s, N_G, rows_pad, N_L;
 };
 
 // Balanced base-512 digits of round(x * 2^(9(s-1) - E)); d[0] is the leading one.
@@ -905,9 +907,9 @@ __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SlicePara
   const SliceJob J = P.job[blockIdx.y];
   const int g = blockIdx.x;
   const int s = P.s;
-  const int kpad = J.nblk * P.P;
+  const int K = J.nblk * P.N_L;                  // complex rows of the source
+  const int kpad = ((2 * K + KB - 1) / KB) * KB;  // packed real K, whole 16-wide blocks
   const size_t slice_elems = (size_t)P.rows_pad * kpad;
-  const int hp = P.P / 2;  // complex positions per block
   __shared__ double red[32];
   __shared__ int s_E;
   const int kc = kpad / 2;  // complex positions per padded row
@@ -922,7 +924,6 @@ __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SlicePara
     return;
   }
   const double2* col = J.X + (size_t)g * J.ldX;
-  const int K = J.nblk * P.N_L;
   double m = 0.0;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double2 v = col[k];
@@ -941,15 +942,13 @@ __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SlicePara
   __syncthreads();
   const int E = s_E;
   for (int j = threadIdx.x; j < kc; j += blockDim.x) {
-    const int blk = j / hp, l = j - blk * hp;
-    const bool zero = (l >= P.N_L);
+    const bool zero = (j >= K);
     double2 v = make_double2(0.0, 0.0);
     if (!zero) {
-      const int k = blk * P.N_L + l;
-      v = col[k];
+      v = col[j];
       if (J.u) {
-        v.x *= J.u[k];
-        v.y *= J.u[k];
+        v.x *= J.u[j];
+        v.y *= J.u[j];
       }
     }
     put_slices(v, zero, E, s, J.plain, J.rot, slice_elems, tile_off(g, j, NKB));
@@ -958,7 +957,10 @@ __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SlicePara
 
 // Slices of the per-atom operators (k-independent, once per factorisation):
 // job 0: MZ[a] (N_L x 2N_L), K = [A part | B part] = 2P; job 1: M2[a] (N_L x N_L),
-// K = P.  Real row n = 2L + c of output row L: c = 0 gives Re, c = 1 gives Im:
+// K = P, P = the widest K block range of an atom in the packed coefficient layout.
+// Column l of a part sits at real position (2 a N_L) mod 16 + 2l, the offset of
+// atom a's rows inside its first K block, zeros elsewhere.  Real row n = 2L + c of
+// output row L: c = 0 gives Re, c = 1 gives Im:
 //   row 2L:   (Re M(L,k), -Im M(L,k)) pairs;   row 2L+1: (Im M(L,k), Re M(L,k)).
 // Layout [a][p][n_pad][Kop]; one exponent per (a, n), shared by rows 2L, 2L+1.
 __global__ void __launch_bounds__(128) k_slice_op(const double2* __restrict__ M, int job, int N_A,
@@ -992,9 +994,10 @@ __global__ void __launch_bounds__(128) k_slice_op(const double2* __restrict__ M,
   __syncthreads();
   const int E = s_E;
   const int hp = P / 2;
+  const int oc = ((2 * a * N_L) & (KB - 1)) >> 1;  // complex offset of atom a in its K block
   for (int j = threadIdx.x; j < Kop / 2; j += blockDim.x) {
-    const int part = j / hp, l = j - part * hp;
-    const bool zero = (L >= N_L) || (l >= N_L);
+    const int part = j / hp, l = j - part * hp - oc;
+    const bool zero = (L >= N_L) || (l < 0) || (l >= N_L);
     double2 v = make_double2(0.0, 0.0);
     if (!zero) {
       const double2 mv = Ma[L + (size_t)(part * N_L + l) * ldM];
@@ -1039,8 +1042,16 @@ bool encode_tiles(CUtensorMap* m, const uint16_t* base, int NKB, int NRB, int pl
 }  // namespace
 
 static inline int rows_pad_of(int N_G) { return ((N_G + ROWS_ALIGN - 1) / ROWS_ALIGN) * ROWS_ALIGN; }
-// Padded real length of one block of N_L complex rows (multiple of KB: 32 bytes).
-static inline int block_pad(int N_L) { return ((2 * N_L + KB - 1) / KB) * KB; }
+// Packed real K of a source of nblk blocks of N_L complex rows (whole 16-wide blocks).
+static inline int kpad_of(int nblk, int N_L) { return ((2 * nblk * N_L + KB - 1) / KB) * KB; }
+// Real K of one part of a per-atom operator: the most 16-wide K blocks any atom's
+// rows [2 a N_L, 2 (a+1) N_L) of the packed layout touch.
+static int op_part_k(int N_A, int N_L) {
+  int nkb = 0;
+  for (int a = 0; a < N_A; ++a)
+    nkb = std::max(nkb, (2 * (a + 1) * N_L + KB - 1) / KB - (2 * a * N_L) / KB);
+  return nkb * KB;
+}
 // Operator rows (2 N_L real rows) padded to whole 128-row MMA tiles.
 static inline int op_rows_pad(int N_L) { return ((2 * N_L + BN - 1) / BN) * BN; }
 
@@ -1054,13 +1065,12 @@ size_t hs_plan_s::split_ws_bytes(int N_G, int n_fail) const {
   if (precision != HS_SPLIT_BF16) return 0;
   const int nf = n_fail > 0 ? n_fail : 1;
   const int rp = rows_pad_of(N_G);
-  const size_t P = (size_t)block_pad(N_L);
   size_t b = 0;
   for (int src = 0; src < NSRC; ++src) {
     int nblk;
     bool rot;
     source_shape(src, N_A, nf, nblk, rot);
-    const size_t one = (size_t)slices * rp * nblk * P * 2;
+    const size_t one = (size_t)slices * rp * kpad_of(nblk, N_L) * 2;
     b += (rot ? 2 : 1) * one + sizeof(int) * rp;
   }
   return b;
@@ -1070,7 +1080,6 @@ int hs_plan_s::split_ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st
   if (precision != HS_SPLIT_BF16) return HS_OK;
   if (!get_encode()) return HS_ECUDA;
   const int rp = rows_pad_of(N_G);
-  const size_t P = (size_t)block_pad(N_L);
   auto al = [&](void** ptr, size_t bytes) -> bool {
     return (async ? hs_malloc_async(ptr, bytes, st, hs_serve_pool(this)) : cudaMalloc(ptr, bytes)) ==
            cudaSuccess;
@@ -1079,7 +1088,7 @@ int hs_plan_s::split_ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st
     int nblk;
     bool rot;
     source_shape(src, N_A, n_fail, nblk, rot);
-    const size_t one = (size_t)slices * rp * nblk * P * 2;
+    const size_t one = (size_t)slices * rp * kpad_of(nblk, N_L) * 2;
     if (!al((void**)&w.sb[src].plain, one)) return HS_ENOMEM;
     if (rot && !al((void**)&w.sb[src].rot, one)) return HS_ENOMEM;
     if (!al((void**)&w.sb[src].expo, sizeof(int) * rp)) return HS_ENOMEM;
@@ -1089,14 +1098,14 @@ int hs_plan_s::split_ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st
 
 size_t hs_plan_s::split_fixed_bytes() const {
   if (precision != HS_SPLIT_BF16) return 0;
-  const size_t P = (size_t)block_pad(N_L), np = (size_t)op_rows_pad(N_L);
+  const size_t P = (size_t)op_part_k(N_A, N_L), np = (size_t)op_rows_pad(N_L);
   return (size_t)N_A * slices * np * (3 * P) * 2 + 2 * sizeof(int) * N_A * np;
 }
 
 int hs_plan_s::split_plan_alloc() {
   if (precision != HS_SPLIT_BF16) return HS_OK;
   if (!get_encode()) return HS_ECUDA;
-  const size_t P = (size_t)block_pad(N_L), np = (size_t)op_rows_pad(N_L);
+  const size_t P = (size_t)op_part_k(N_A, N_L), np = (size_t)op_rows_pad(N_L);
   const size_t zb = (size_t)N_A * slices * np * 2 * P * 2, wb = zb / 2;
   if (cudaMalloc((void**)&op_slices[0], zb) != cudaSuccess ||
       cudaMalloc((void**)&op_slices[1], wb) != cudaSuccess ||
@@ -1120,7 +1129,7 @@ void hs_plan_s::split_plan_release() {
 // Slice MZ and M2 (k-independent) after every factorisation.
 int hs_plan_s::split_factor(cudaStream_t st) {
   if (precision != HS_SPLIT_BF16) return HS_OK;
-  const int P = block_pad(N_L), np = op_rows_pad(N_L);
+  const int P = op_part_k(N_A, N_L), np = op_rows_pad(N_L);
   k_slice_op<<<dim3(np, N_A), 128, 0, st>>>(MZ, 0, N_A, N_L, P, np, slices, op_slices[0],
                                              op_expo[0]);
   HS_CUDA_TRY(cudaGetLastError());
@@ -1348,13 +1357,12 @@ static void slice_job(SliceParams& sp, int& nj, Workspace& w, int src, const dou
   sp.job[nj++] = SliceJob{X, u, b.plain, b.rot, b.expo, ldX, nblk};
 }
 
-static int slice_launch(SliceParams& sp, int nj, int s, int N_G, int rp, int N_L, int Pp,
+static int slice_launch(SliceParams& sp, int nj, int s, int N_G, int rp, int N_L,
                         cudaStream_t st) {
   sp.s = s;
   sp.N_G = N_G;
   sp.rows_pad = rp;
   sp.N_L = N_L;
-  sp.P = Pp;
   k_slice<<<dim3(rp, nj), 256, 0, st>>>(sp);
   return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
 }
@@ -1369,7 +1377,7 @@ int hs_plan_s::split_inputs(const double2* A, const double2* B, int ldAB, const 
   slice_job(sp, nj, w, SRC_A, A, ldAB, N_A, nullptr);
   slice_job(sp, nj, w, SRC_UB, B, ldAB, N_A, U);
   slice_job(sp, nj, w, SRC_B, B, ldAB, N_A, nullptr);
-  return slice_launch(sp, nj, slices, N_G, rp, N_L, block_pad(N_L), st);
+  return slice_launch(sp, nj, slices, N_G, rp, N_L, st);
 }
 
 // 2. per-atom products of up to kMaxBatch k-points in one grouped launch: Z and
@@ -1377,7 +1385,7 @@ int hs_plan_s::split_inputs(const double2* A, const double2* B, int ldAB, const 
 //    node of the plan's captured graph.
 int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGraph* graph) {
   if (n < 1 || n > kMaxBatch) return HS_EINVAL;
-  const int s = slices, Pp = block_pad(N_L), np = op_rows_pad(N_L);
+  const int s = slices, Pp = op_part_k(N_A, N_L), np = op_rows_pad(N_L);
   int n_stage;
   size_t smem;
   int rc = split_geometry(n_stage, smem);
@@ -1397,8 +1405,9 @@ int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGr
     AtomsReq& R = at.rq[r];
     R.mA = 2 + 2 * r;
     R.mB = 3 + 2 * r;
-    ok = encode_tiles(&PA->maps[R.mA], w.sb[SRC_A].plain, N_A * Pp / KB, rp / 64, s) &&
-         encode_tiles(&PA->maps[R.mB], w.sb[SRC_B].plain, N_A * Pp / KB, rp / 64, s);
+    const int nkb = kpad_of(N_A, N_L) / KB;
+    ok = encode_tiles(&PA->maps[R.mA], w.sb[SRC_A].plain, nkb, rp / 64, s) &&
+         encode_tiles(&PA->maps[R.mB], w.sb[SRC_B].plain, nkb, rp / 64, s);
     R.eA = w.sb[SRC_A].expo;
     R.eB = w.sb[SRC_B].expo;
     R.Z = w.Z;
@@ -1446,7 +1455,6 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   const int N_h = N_A - N_f;
   const int s = slices;
   const int rp = rows_pad_of(N_G);
-  const int Pp = block_pad(N_L);
   int n_stage;
   size_t smem;
   int rc = split_geometry(n_stage, smem);
@@ -1462,7 +1470,7 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
       slice_job(sp, nj, w, SRC_AF, w.AF, N_f * N_L, N_f, nullptr);
       slice_job(sp, nj, w, SRC_X, w.W2 + (size_t)N_h * N_L, K, N_f, nullptr);
     }
-    rc = slice_launch(sp, nj, s, N_G, rp, N_L, Pp, st);
+    rc = slice_launch(sp, nj, s, N_G, rp, N_L, st);
     if (rc) return rc;
   }
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[5], st));
@@ -1476,10 +1484,10 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   auto add_map = [&](int src, int nblk) -> bool {
     SliceBuf& b = w.sb[src];
     map_of[src][0] = nm;
-    if (!encode_tiles(&P.maps[nm++], b.plain, nblk * Pp / KB, rp / 64, s)) return false;
+    if (!encode_tiles(&P.maps[nm++], b.plain, kpad_of(nblk, N_L) / KB, rp / 64, s)) return false;
     if (b.rot) {
       map_of[src][1] = nm;
-      if (!encode_tiles(&P.maps[nm++], b.rot, nblk * Pp / KB, rp / 64, s)) return false;
+      if (!encode_tiles(&P.maps[nm++], b.rot, kpad_of(nblk, N_L) / KB, rp / 64, s)) return false;
     }
     return true;
   };
@@ -1508,7 +1516,7 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
     g.mL = map_of[srcL][0];
     g.mR = map_of[srcR][0];
     g.mRr = map_of[srcR][1];
-    g.kblocks = nblk * Pp / KB;
+    g.kblocks = kpad_of(nblk, N_L) / KB;
     g.eL = w.sb[srcL].expo;
     g.eR = w.sb[srcR].expo;
     return g;
