@@ -60,9 +60,16 @@ constexpr int TILE_BYTES = 64 * KB * 2;  // one 64-row TMA box: 2 KB
 constexpr int NUM_DRAIN_WARPS = 16;     // four per TMEM lane quarter
 constexpr int NUM_THREADS = 64 + 32 * NUM_DRAIN_WARPS;  // warp 0 TMA, warp 1 MMA, then drain
 constexpr uint64_t kWaitNs = 2000000000ull;  // bounded waits: 2 s
-// epilogue staging in the (then idle) stage area: (hi, lo) float2 for 128 rows x
-// 2 strips x 64 columns, plus 128 row and 128 column exponents
-constexpr int STAGING_BYTES = 2 * 64 * 128 * 8 + 256 * 4;
+// epilogue staging in the (then idle) stage area, plus 128 row and 128 column
+// exponents: a contraction stages (hi, lo) float2 as [2 strips x 64 columns][128 rows];
+// the per-atom products stage (hi, lo) of Re and Im as one float4 per (output row L,
+// tile row g), [64 L][ATOMS_ROWP], the pitch of 129 keeping both the drain's writes
+// (consecutive g) and the epilogue's reads (consecutive L) free of bank conflicts
+constexpr int ATOMS_ROWP = 129;
+constexpr int STAGE_VALS_CONTRACT = 2 * 64 * 128 * 8;
+constexpr int STAGE_VALS_ATOMS = 64 * ATOMS_ROWP * 16;
+constexpr int STAGING_BYTES =
+    (STAGE_VALS_ATOMS > STAGE_VALS_CONTRACT ? STAGE_VALS_ATOMS : STAGE_VALS_CONTRACT) + 256 * 4;
 
 // ------------------------------------------------------------------ PTX helpers
 
@@ -297,9 +304,25 @@ __device__ __forceinline__ void drain_window(uint32_t tl, uint32_t mask, f32x2 (
   }
 }
 
-// Exact FP64 power of two (|e| well inside the normal range).
-__device__ __forceinline__ double pow2d(int e) {
-  return __longlong_as_double((long long)(e + 1023) << 52);
+// (hi + lo) * 2^k as FP64, the same value as ((double)hi + (double)lo) * 2^k
+// but with one FP64 instruction instead of four: GB300 issues FP64 at about two per
+// clock per SM, which made the per-atom epilogue (8192 complex results per CTA) longer
+// than its MMAs.  The widening conversions and the power-of-two scaling are exact
+// bit operations (FP32 subnormals take the library conversion; zero, Inf and NaN are
+// left unscaled; |k| stays well inside the exponent range).
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  if (e == 0u && (b & 0x7FFFFFu) != 0u) return (double)f;
+  const uint64_t e64 = e == 0u ? 0u : (e == 0xFFu ? 0x7FFu : e + 896u);
+  return __longlong_as_double((long long)(((uint64_t)(b >> 31) << 63) | (e64 << 52) |
+                                          ((uint64_t)(b & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ double pair_scaled(float hi, float lo, int k) {
+  long long b = __double_as_longlong(f32_to_f64(hi) + f32_to_f64(lo));
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex != 0 && ex != 0x7FF) b += (long long)k << 52;
+  return __longlong_as_double(b);
 }
 
 // ------------------------------------------------------------------ slice-GEMM kernel
@@ -740,18 +763,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
     // stage was consumed by an MMA that completed before the last acc_full):
     // stage (hi, lo) pairs and the last segment's exponents, then write the
     // tile out with consecutive threads on consecutive output addresses.
-    float2* stg = (float2*)smem;                       // [2 strips][64 cols][128 rows]
-    int* s_erow = (int*)(smem + 2 * 64 * 128 * sizeof(float2));
+    float2* stg = (float2*)smem;                       // contraction: [2 strips][64 cols][128 rows]
+    float4* stg4 = (float4*)smem;                      // per-atom: [64 L][ATOMS_ROWP]
+    int* s_erow = (int*)(smem + (MODE == MODE_CONTRACT ? STAGE_VALS_CONTRACT : STAGE_VALS_ATOMS));
     int* s_ecol = s_erow + 128;                        // [2][64]
     const int r = 32 * q4 + lane;
 #pragma unroll
     for (int c = 0; c < 16; c += 2) {
       const float2 ha = unpack2(h0[c >> 1]), la = unpack2(l0[c >> 1]);
       const float2 hb = unpack2(h1[c >> 1]), lb = unpack2(l1[c >> 1]);
-      stg[(0 * 64 + 16 * cg + c) * 128 + r] = make_float2(ha.x, la.x);
-      stg[(0 * 64 + 16 * cg + c + 1) * 128 + r] = make_float2(ha.y, la.y);
-      stg[(1 * 64 + 16 * cg + c) * 128 + r] = make_float2(hb.x, lb.x);
-      stg[(1 * 64 + 16 * cg + c + 1) * 128 + r] = make_float2(hb.y, lb.y);
+      if (MODE == MODE_CONTRACT) {
+        stg[(0 * 64 + 16 * cg + c) * 128 + r] = make_float2(ha.x, la.x);
+        stg[(0 * 64 + 16 * cg + c + 1) * 128 + r] = make_float2(ha.y, la.y);
+        stg[(1 * 64 + 16 * cg + c) * 128 + r] = make_float2(hb.x, lb.x);
+        stg[(1 * 64 + 16 * cg + c + 1) * 128 + r] = make_float2(hb.y, lb.y);
+      } else {  // TMEM columns (2k, 2k + 1) of a strip: Re, Im of local row L
+        const int L0 = 8 * cg + (c >> 1), L1 = 32 + L0;
+        stg4[L0 * ATOMS_ROWP + r] = make_float4(ha.x, la.x, ha.y, la.y);
+        stg4[L1 * ATOMS_ROWP + r] = make_float4(hb.x, lb.x, hb.y, lb.y);
+      }
     }
     if (cg == 0) s_erow[r] = eRow;
     if (q4 == 0 && lane < 16) {
@@ -766,10 +796,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           const int jj = idx >> 7, ii = idx & 127;
           const int i = T.i0 + ii, j = T.j0 + jj;
           if (i < P.N_G && j < P.N_G) {
-            const double sc = pow2d(s_erow[ii] + s_ecol[jj]);
+            const int k = s_erow[ii] + s_ecol[jj];
             const float2 re = stg[jj * 128 + ii], im = stg[(64 + jj) * 128 + ii];
-            P.C[i + (size_t)j * P.ldC] = make_double2(((double)re.x + (double)re.y) * sc,
-                                                      ((double)im.x + (double)im.y) * sc);
+            P.C[i + (size_t)j * P.ldC] = make_double2(pair_scaled(re.x, re.y, k),
+                                                      pair_scaled(im.x, im.y, k));
           }
         }
       } else {
@@ -783,11 +813,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           const int g = T.i0 + gg, L = Lb + ll;
           if (g < T.N_G && L < A.N_L) {
             const int nl = 2 * ll, st = nl >> 6, c = nl & 63;
-            const float2 re = stg[(st * 64 + c) * 128 + gg], im = stg[(st * 64 + c + 1) * 128 + gg];
-            const double sre = pow2d(s_erow[gg] + s_ecol[st * 64 + c]);
-            const double sim = pow2d(s_erow[gg] + s_ecol[st * 64 + c + 1]);
-            out[(size_t)L + (size_t)g * A.ld] = make_double2(((double)re.x + (double)re.y) * sre,
-                                                             ((double)im.x + (double)im.y) * sim);
+            const float4 v = stg4[ll * ATOMS_ROWP + gg];
+            out[(size_t)L + (size_t)g * A.ld] =
+                make_double2(pair_scaled(v.x, v.y, s_erow[gg] + s_ecol[st * 64 + c]),
+                             pair_scaled(v.z, v.w, s_erow[gg] + s_ecol[st * 64 + c + 1]));
           }
         }
       }
@@ -862,6 +891,17 @@ __device__ __forceinline__ uint16_t bf16_bits(float f) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(f));
 }
 
+// |x| as its bit pattern (non-negative doubles order like their bit patterns), 0 for a
+// non-finite x: column maxima are taken with integer instructions, off the FP64 pipe
+// (about two instructions per clock per SM on GB300).
+__device__ __forceinline__ unsigned long long finite_abs_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  return (b >> 52) == 0x7FFull ? 0ull : b;
+}
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7FF) != 0x7FF;
+}
+
 // Exponent E with max / 2^E in [64, 128) (0 for an all-zero or non-finite max).
 __device__ __forceinline__ int slice_exponent(double mm) {
   int e = 0;
@@ -876,7 +916,7 @@ __device__ __forceinline__ int slice_exponent(double mm) {
 __device__ __forceinline__ void put_slices(double2 v, bool zero, int E, int s, uint16_t* plain,
                                            uint16_t* rot, size_t slice_elems, size_t off) {
   int dr[kMaxSlices], di[kMaxSlices];
-  const bool bad = !zero && !(isfinite(v.x) && isfinite(v.y));
+  const bool bad = !zero && !(finite_bits(v.x) && finite_bits(v.y));
   if (!zero) {
     digits_of(v.x, E, s, dr);
     digits_of(v.y, E, s, di);
@@ -910,7 +950,7 @@ __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SlicePara
   const int K = J.nblk * P.N_L;                  // complex rows of the source
   const int kpad = ((2 * K + KB - 1) / KB) * KB;  // packed real K, whole 16-wide blocks
   const size_t slice_elems = (size_t)P.rows_pad * kpad;
-  __shared__ double red[32];
+  __shared__ unsigned long long red[32];
   __shared__ int s_E;
   const int kc = kpad / 2;  // complex positions per padded row
   const int NKB = kpad / KB;
@@ -924,19 +964,20 @@ __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SlicePara
     return;
   }
   const double2* col = J.X + (size_t)g * J.ldX;
-  double m = 0.0;
+  unsigned long long m = 0ull;  // bit pattern of the column's largest finite |component| (x |u|)
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    double2 v = col[k];
-    const double w = J.u ? fabs(J.u[k]) : 1.0;
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)) * w);
+    const double2 v = col[k];
+    unsigned long long a = max(finite_abs_bits(v.x), finite_abs_bits(v.y));
+    if (J.u) a = finite_abs_bits(__longlong_as_double((long long)a) * fabs(J.u[k]));
+    m = max(m, a);
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double mm = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = fmax(mm, red[i]);
-    s_E = slice_exponent(mm);
+    unsigned long long mm = 0ull;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = max(mm, red[i]);
+    s_E = slice_exponent(__longlong_as_double((long long)mm));
     J.expo[g] = s_E;
   }
   __syncthreads();
