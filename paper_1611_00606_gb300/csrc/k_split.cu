@@ -887,8 +887,15 @@ __device__ __forceinline__ void digits_of(double x, int E, int s, int (&d)[kMaxS
   d[0] = (int)Y;
 }
 
-__device__ __forceinline__ uint16_t bf16_bits(float f) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+// BF16 bits of d * sc for a digit |d| <= 256 and sc = 2^-9p: the value has at most 8
+// significant bits, so it is exact in BF16 and its BF16 bits are the upper half of its
+// FP32 bits.  d converts with the 1.5 * 2^23 magic number (FP32 add, exact for
+// |d| < 2^22) instead of an int-to-float conversion: the slicer writes 20 BF16 values
+// per complex entry and the conversion units (a quarter of the FP32 rate) were its
+// limit.
+__device__ __forceinline__ uint32_t bf16_digit(int d, float sc) {
+  const float f = (__int_as_float(0x4B400000 + d) - 12582912.0f) * sc;
+  return __float_as_uint(f) >> 16;
 }
 
 // |x| as its bit pattern (non-negative doubles order like their bit patterns), 0 for a
@@ -932,10 +939,9 @@ __device__ __forceinline__ void put_slices(double2 v, bool zero, int E, int s, u
       if (bad) {
         pl = rt = 0x7FC07FC0u;  // NaN pair: propagates through the MMA
       } else {
-        pl = (uint32_t)bf16_bits((float)dr[p] * sc) |
-             ((uint32_t)bf16_bits((float)di[p] * sc) << 16);
-        rt = (uint32_t)bf16_bits((float)di[p] * sc) |
-             ((uint32_t)bf16_bits((float)(-dr[p]) * sc) << 16);
+        const uint32_t br = bf16_digit(dr[p], sc), bi = bf16_digit(di[p], sc);
+        pl = br | (bi << 16);
+        rt = bi | ((br == 0u ? 0u : br ^ 0x8000u) << 16);  // -dr: sign flip (zero stays +0)
       }
       *(uint32_t*)(plain + p * slice_elems + off) = pl;
       if (rot) *(uint32_t*)(rot + p * slice_elems + off) = rt;
