@@ -60,17 +60,9 @@ constexpr int TILE_BYTES = 64 * KB * 2;  // one 64-row TMA box: 2 KB
 constexpr int NUM_DRAIN_WARPS = 16;     // four per TMEM lane quarter
 constexpr int NUM_THREADS = 64 + 32 * NUM_DRAIN_WARPS;  // warp 0 TMA, warp 1 MMA, then drain
 constexpr uint64_t kWaitNs = 2000000000ull;  // bounded waits: 2 s
-// epilogue staging in the (then idle) stage area, plus 128 row and 128 column
-// exponents: a contraction stages (hi, lo) float2 as [2 strips x 64 columns][128 rows];
-// the per-atom products stage (hi, lo) of Re and Im as one float4 per (output row L,
-// tile row g), [64 L][ATOMS_ROWP], the pitch of 129 keeping both the drain's writes
-// (consecutive g) and the epilogue's reads (consecutive L) free of bank conflicts
-constexpr int ATOMS_ROWP = 129;
-constexpr int STAGE_VALS_CONTRACT = 2 * 64 * 128 * 8;
-constexpr int STAGE_VALS_ATOMS = 64 * ATOMS_ROWP * 16;
-constexpr int STAGING_BYTES =
-    (STAGE_VALS_ATOMS > STAGE_VALS_CONTRACT ? STAGE_VALS_ATOMS : STAGE_VALS_CONTRACT) + 256 * 4;
-
+// contraction epilogue staging in the (then idle) stage ring: (hi, lo) float2 as
+// [2 strips x 64 columns][128 rows], plus 128 row and 128 column exponents
+constexpr int STAGING_CONTRACT = 2 * 64 * 128 * 8 + 256 * 4;
 // ------------------------------------------------------------------ PTX helpers
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -380,6 +372,7 @@ struct SplitParams {
   int n_stage;    // pipeline depth
   int N_G, ldC, nbj;
   int nbi, band;   // contraction: 128-row blocks, row blocks per band of the tile order
+  int ntiles;      // tiles of the launch; a CTA runs tiles blockIdx.x, + gridDim.x, ...
   int rows_pad;   // slice p of a coefficient-side array starts at row p * rows_pad
   double2* C;
   int* err;
@@ -409,7 +402,7 @@ struct TileId {
 };
 
 template <int MODE>
-__device__ __forceinline__ TileId decode_tile(const SplitParams& P) {
+__device__ __forceinline__ TileId decode_tile(const SplitParams& P, int tile) {
   TileId t{};
   if (MODE == MODE_CONTRACT) {
     // Clusters of two CTAs: column blocks 2c and 2c + 1 of one row block (which
@@ -419,7 +412,7 @@ __device__ __forceinline__ TileId decode_tile(const SplitParams& P) {
     // band) and column-major inside a band, so the CTAs resident at one time
     // cover a compact block of rows x columns and share their operand tiles in L2.
     const int npr = (P.nbj + 1) >> 1;
-    int p = blockIdx.x >> 1, bi = 0, c = 0;
+    int p = tile >> 1, bi = 0, c = 0;
     for (int b0 = 0; b0 < P.nbi; b0 += P.band) {
       const int b1 = min(b0 + P.band, P.nbi);
       int n = 0;
@@ -443,9 +436,9 @@ __device__ __forceinline__ TileId decode_tile(const SplitParams& P) {
     t.N_G = P.N_G;
   } else {
     int r = 0;
-    while (r + 1 < P.at.nreq && (int)blockIdx.x >= P.at.rq[r + 1].tile0) ++r;
+    while (r + 1 < P.at.nreq && tile >= P.at.rq[r + 1].tile0) ++r;
     const AtomsReq& R = P.at.rq[r];
-    int b = blockIdx.x - R.tile0;
+    int b = tile - R.tile0;
     t.r = r;
     t.N_G = R.N_G;
     const int gb = b % R.ngblk;
@@ -548,7 +541,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   const int NS = P.n_stage;
   const uint32_t a_bytes = (uint32_t)s * 2 * TILE_BYTES;   // s slices x 128 rows
   const uint32_t stage_bytes = 2 * a_bytes;                 // A part + B part
-  const uint32_t ring_bytes = max(NS * stage_bytes, (uint32_t)STAGING_BYTES);
+  const uint32_t ring_bytes =
+      MODE == MODE_CONTRACT ? max(NS * stage_bytes, (uint32_t)STAGING_CONTRACT) : NS * stage_bytes;
   uint64_t* full = (uint64_t*)(smem + ring_bytes);
   uint64_t* empty = full + NS;
   uint64_t* acc_full = empty + NS;
@@ -557,7 +551,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
-  const TileId T = decode_tile<MODE>(P);
+  const TileId T0 = decode_tile<MODE>(P, blockIdx.x);  // first tile (tensor-map prefetch)
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < NS; ++i) {
@@ -572,8 +566,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 0 && lane == 0)
-    for (int sg = 0; sg < T.nseg; ++sg) {
-      const SegInfo si = seg_info<MODE>(P, T, sg);
+    for (int sg = 0; sg < T0.nseg; ++sg) {
+      const SegInfo si = seg_info<MODE>(P, T0, sg);
       prefetch_map(si.mL);
       prefetch_map(si.mR1);
       prefetch_map(si.mR2);
@@ -601,7 +595,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
     bool ok = true;
     const int bp = lane / NB, bk = lane - bp * NB;  // this lane's slice and box kind
     const int h = (int)cluster_rank();
-    for (int sg = 0; sg < T.nseg && ok; ++sg) {
+    for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
+     const TileId T = decode_tile<MODE>(P, tile);
+     for (int sg = 0; sg < T.nseg && ok; ++sg) {
       const SegInfo si = seg_info<MODE>(P, T, sg);
       for (int kb = 0; kb < si.kblocks; ++kb) {
         if (lane == 0) {
@@ -637,6 +633,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           phase ^= 1u;
         }
       }
+     }
     }
     if (lane == 0) {
       if (!ok) {
@@ -666,7 +663,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
       uint32_t phase = 0;
       int nwin = 0;
       bool ok = true;
-      for (int sg = 0; sg < T.nseg && ok; ++sg) {
+      for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
+       const TileId T = decode_tile<MODE>(P, tile);
+       for (int sg = 0; sg < T.nseg && ok; ++sg) {
         const int kbn = seg_info<MODE>(P, T, sg).kblocks;
         uint32_t restart = 0xFu;  // accumulators to restart in the next window
         for (int w0 = 0; w0 < kbn && ok; w0 += WIN) {
@@ -697,6 +696,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           if (ok) tc_commit(acc_full);
           ++nwin;
         }
+       }
       }
       if (!ok) {
         atomicExch(P.err, 2);
@@ -709,89 +709,80 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
         if (globaltimer() - t0 > kWaitNs) break;
     }
   } else {
-    // ---------------- drain warps: TMEM -> double-float accumulators
+    // ---------------- drain warps: TMEM -> double-float accumulators, then the tile's
+    // results straight from registers (the next tile's MMAs start as soon as the last
+    // read-out has released the accumulators, so these stores overlap them)
     const int q4 = warp & 3;         // TMEM lane quarter this warp may access
     const int cg = (warp - 2) >> 2;  // 16-column group of each 64-column strip
-    const int row = T.i0 + 32 * q4 + lane;
     const uint32_t tl = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(16 * cg);
-    f32x2 h0[8], l0[8], h1[8], l1[8];  // column pairs of strip 0 (TMEM cols < 64), strip 1
-#pragma unroll
-    for (int c = 0; c < 8; ++c) h0[c] = l0[c] = h1[c] = l1[c] = 0ull;
     int nwin = 0;
     bool ok = true;
-    int eRow = 0, eC0 = 0, eC1 = 0;  // current segment's exponents (lane c: column c)
-    for (int sg = 0; sg < T.nseg && ok; ++sg) {
-      const SegInfo si = seg_info<MODE>(P, T, sg);
-      const int nRow = si.eRow[row];
-      const int nC0 = si.eC0[16 * cg + (lane & 15)];
-      const int nC1 = si.eC1[16 * cg + (lane & 15)];
-      if (sg > 0) {  // move the pairs into the new segment's units (exact powers of two)
+    for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
+      const TileId T = decode_tile<MODE>(P, tile);
+      const int row = T.i0 + 32 * q4 + lane;
+      f32x2 h0[8], l0[8], h1[8], l1[8];  // column pairs of strip 0 (TMEM cols < 64), strip 1
+#pragma unroll
+      for (int c = 0; c < 8; ++c) h0[c] = l0[c] = h1[c] = l1[c] = 0ull;
+      int eRow = 0, eC0 = 0, eC1 = 0;  // current segment's exponents (lane c: column c)
+      for (int sg = 0; sg < T.nseg && ok; ++sg) {
+        const SegInfo si = seg_info<MODE>(P, T, sg);
+        const int nRow = si.eRow[row];
+        const int nC0 = si.eC0[16 * cg + (lane & 15)];
+        const int nC1 = si.eC1[16 * cg + (lane & 15)];
+        if (sg > 0) {  // move the pairs into the new segment's units (exact powers of two)
+#pragma unroll
+          for (int c = 0; c < 16; c += 2) {
+            const int dr = eRow - nRow;
+            const f32x2 f0 = pack2(pow2f(dr + __shfl_sync(0xffffffffu, eC0 - nC0, c)),
+                                   pow2f(dr + __shfl_sync(0xffffffffu, eC0 - nC0, c + 1)));
+            const f32x2 f1 = pack2(pow2f(dr + __shfl_sync(0xffffffffu, eC1 - nC1, c)),
+                                   pow2f(dr + __shfl_sync(0xffffffffu, eC1 - nC1, c + 1)));
+            h0[c >> 1] = mul2(h0[c >> 1], f0);
+            l0[c >> 1] = mul2(l0[c >> 1], f0);
+            h1[c >> 1] = mul2(h1[c >> 1], f1);
+            l1[c >> 1] = mul2(l1[c >> 1], f1);
+          }
+        }
+        eRow = nRow;
+        eC0 = nC0;
+        eC1 = nC1;
+        for (int w0 = 0; w0 < si.kblocks; w0 += WIN) {
+          if (!mbar_wait(acc_full, (uint32_t)nwin & 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          drain_window<S>(tl, due_mask(w0 / WIN, w0 + WIN >= si.kblocks), h0, l0, h1, l1);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acc_empty);
+          ++nwin;
+        }
+      }
+      if (!ok || *abort_flag) break;
+      // Results: (hi + lo) * 2^(E_row + E_col) in FP64.  Thread = one tile row; pair k
+      // of a strip = its TMEM columns 16 cg + 2k and 2k + 1 (lanes 2k, 2k + 1 of eC*).
+      if (MODE == MODE_CONTRACT) {
+        // one tile per CTA: stage (hi, lo) in the idle ring (every stage was consumed by
+        // an MMA that completed before the last acc_full), then write the tile with
+        // consecutive threads on consecutive output addresses
+        float2* stg = (float2*)smem;  // [2 strips][64 cols][128 rows]
+        int* s_erow = (int*)(smem + 2 * 64 * 128 * sizeof(float2));
+        int* s_ecol = s_erow + 128;   // [64]
+        const int r = 32 * q4 + lane;
 #pragma unroll
         for (int c = 0; c < 16; c += 2) {
-          const int dr = eRow - nRow;
-          const f32x2 f0 = pack2(pow2f(dr + __shfl_sync(0xffffffffu, eC0 - nC0, c)),
-                                 pow2f(dr + __shfl_sync(0xffffffffu, eC0 - nC0, c + 1)));
-          const f32x2 f1 = pack2(pow2f(dr + __shfl_sync(0xffffffffu, eC1 - nC1, c)),
-                                 pow2f(dr + __shfl_sync(0xffffffffu, eC1 - nC1, c + 1)));
-          h0[c >> 1] = mul2(h0[c >> 1], f0);
-          l0[c >> 1] = mul2(l0[c >> 1], f0);
-          h1[c >> 1] = mul2(h1[c >> 1], f1);
-          l1[c >> 1] = mul2(l1[c >> 1], f1);
+          const float2 ha = unpack2(h0[c >> 1]), la = unpack2(l0[c >> 1]);
+          const float2 hb = unpack2(h1[c >> 1]), lb = unpack2(l1[c >> 1]);
+          stg[(0 * 64 + 16 * cg + c) * 128 + r] = make_float2(ha.x, la.x);
+          stg[(0 * 64 + 16 * cg + c + 1) * 128 + r] = make_float2(ha.y, la.y);
+          stg[(1 * 64 + 16 * cg + c) * 128 + r] = make_float2(hb.x, lb.x);
+          stg[(1 * 64 + 16 * cg + c + 1) * 128 + r] = make_float2(hb.y, lb.y);
         }
-      }
-      eRow = nRow;
-      eC0 = nC0;
-      eC1 = nC1;
-      for (int w0 = 0; w0 < si.kblocks; w0 += WIN) {
-        if (!mbar_wait(acc_full, (uint32_t)nwin & 1u, abort_flag)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        drain_window<S>(tl, due_mask(w0 / WIN, w0 + WIN >= si.kblocks), h0, l0, h1, l1);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(acc_empty);
-        ++nwin;
-      }
-    }
-    if (!ok) {
-      atomicExch(P.err, 3);
-      *abort_flag = 1;
-    }
-    // Epilogue through shared memory (the pipeline stages are idle now: every
-    // stage was consumed by an MMA that completed before the last acc_full):
-    // stage (hi, lo) pairs and the last segment's exponents, then write the
-    // tile out with consecutive threads on consecutive output addresses.
-    float2* stg = (float2*)smem;                       // contraction: [2 strips][64 cols][128 rows]
-    float4* stg4 = (float4*)smem;                      // per-atom: [64 L][ATOMS_ROWP]
-    int* s_erow = (int*)(smem + (MODE == MODE_CONTRACT ? STAGE_VALS_CONTRACT : STAGE_VALS_ATOMS));
-    int* s_ecol = s_erow + 128;                        // [2][64]
-    const int r = 32 * q4 + lane;
-#pragma unroll
-    for (int c = 0; c < 16; c += 2) {
-      const float2 ha = unpack2(h0[c >> 1]), la = unpack2(l0[c >> 1]);
-      const float2 hb = unpack2(h1[c >> 1]), lb = unpack2(l1[c >> 1]);
-      if (MODE == MODE_CONTRACT) {
-        stg[(0 * 64 + 16 * cg + c) * 128 + r] = make_float2(ha.x, la.x);
-        stg[(0 * 64 + 16 * cg + c + 1) * 128 + r] = make_float2(ha.y, la.y);
-        stg[(1 * 64 + 16 * cg + c) * 128 + r] = make_float2(hb.x, lb.x);
-        stg[(1 * 64 + 16 * cg + c + 1) * 128 + r] = make_float2(hb.y, lb.y);
-      } else {  // TMEM columns (2k, 2k + 1) of a strip: Re, Im of local row L
-        const int L0 = 8 * cg + (c >> 1), L1 = 32 + L0;
-        stg4[L0 * ATOMS_ROWP + r] = make_float4(ha.x, la.x, ha.y, la.y);
-        stg4[L1 * ATOMS_ROWP + r] = make_float4(hb.x, lb.x, hb.y, lb.y);
-      }
-    }
-    if (cg == 0) s_erow[r] = eRow;
-    if (q4 == 0 && lane < 16) {
-      s_ecol[16 * cg + lane] = eC0;
-      s_ecol[64 + 16 * cg + lane] = eC1;
-    }
-    asm volatile("bar.sync 1, %0;" ::"r"(32 * NUM_DRAIN_WARPS) : "memory");
-    const int dt = threadIdx.x - 64;  // 0 .. 32*NUM_DRAIN_WARPS-1
-    if (ok && !*abort_flag) {
-      if (MODE == MODE_CONTRACT) {
+        if (cg == 0) s_erow[r] = eRow;
+        if (q4 == 0 && lane < 16) s_ecol[16 * cg + lane] = eC0;
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * NUM_DRAIN_WARPS) : "memory");
+        const int dt = threadIdx.x - 64;  // 0 .. 32*NUM_DRAIN_WARPS-1
         for (int idx = dt; idx < 64 * 128; idx += 32 * NUM_DRAIN_WARPS) {
           const int jj = idx >> 7, ii = idx & 127;
           const int i = T.i0 + ii, j = T.j0 + jj;
@@ -803,23 +794,36 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           }
         }
       } else {
+        // columns (2k, 2k + 1) of a strip = Re, Im of output row L: strip 0 holds
+        // L = 8 cg + k, strip 1 L + 32; each thread writes 8 consecutive complex
+        // values (128 contiguous bytes) per strip
         const AtomsArgs& A = P.at;
         const AtomsReq& R = A.rq[T.r];
         double2* out = T.job == 0 ? R.Z + (size_t)T.a * A.N_L
                                   : R.W2 + (size_t)A.slot[T.a] * A.N_L;
-        const int Lb = T.n0 >> 1;
-        for (int idx = dt; idx < 64 * 128; idx += 32 * NUM_DRAIN_WARPS) {
-          const int gg = idx >> 6, ll = idx & 63;  // tile row, local output row
-          const int g = T.i0 + gg, L = Lb + ll;
-          if (g < T.N_G && L < A.N_L) {
-            const int nl = 2 * ll, st = nl >> 6, c = nl & 63;
-            const float4 v = stg4[ll * ATOMS_ROWP + gg];
-            out[(size_t)L + (size_t)g * A.ld] =
-                make_double2(pair_scaled(v.x, v.y, s_erow[gg] + s_ecol[st * 64 + c]),
-                             pair_scaled(v.z, v.w, s_erow[gg] + s_ecol[st * 64 + c + 1]));
-          }
+        const int g = row;
+        const int Lb = (T.n0 >> 1) + 8 * cg;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int e0r = eRow + __shfl_sync(0xffffffffu, eC0, 2 * k);
+          const int e0i = eRow + __shfl_sync(0xffffffffu, eC0, 2 * k + 1);
+          const int e1r = eRow + __shfl_sync(0xffffffffu, eC1, 2 * k);
+          const int e1i = eRow + __shfl_sync(0xffffffffu, eC1, 2 * k + 1);
+          const float2 ha = unpack2(h0[k]), la = unpack2(l0[k]);
+          const float2 hb = unpack2(h1[k]), lb = unpack2(l1[k]);
+          const int L0 = Lb + k, L1 = Lb + 32 + k;
+          if (g < T.N_G && L0 < A.N_L)
+            out[(size_t)L0 + (size_t)g * A.ld] =
+                make_double2(pair_scaled(ha.x, la.x, e0r), pair_scaled(ha.y, la.y, e0i));
+          if (g < T.N_G && L1 < A.N_L)
+            out[(size_t)L1 + (size_t)g * A.ld] =
+                make_double2(pair_scaled(hb.x, lb.x, e1r), pair_scaled(hb.y, lb.y, e1i));
         }
       }
+    }
+    if (!ok) {
+      atomicExch(P.err, 3);
+      *abort_flag = 1;
     }
   }
 
@@ -1332,8 +1336,9 @@ void tune_store_locked(const std::string& key, int v) {
   std::fclose(f);
 }
 
-size_t smem_for(int n_stage, int stage_bytes) {
-  return std::max((size_t)n_stage * stage_bytes, (size_t)STAGING_BYTES) + 1024 + 256;
+size_t smem_for(int mode, int n_stage, int stage_bytes) {
+  const size_t ring = (size_t)n_stage * stage_bytes;
+  return (mode == MODE_CONTRACT ? std::max(ring, (size_t)STAGING_CONTRACT) : ring) + 1024 + 256;
 }
 
 // Depth for this launch; `trial(depth)` enqueues the real work with that depth.
@@ -1394,7 +1399,7 @@ int hs_plan_s::split_geometry(int& n_stage, size_t& smem) const {
   n_stage = budget / stage_bytes;
   if (n_stage > 8) n_stage = 8;
   if (n_stage < 2) return HS_EINVAL;
-  smem = smem_for(n_stage, stage_bytes);
+  smem = smem_for(MODE_CONTRACT, n_stage, stage_bytes);
   return HS_OK;
 }
 
@@ -1469,6 +1474,17 @@ int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGr
     return HS_ECUDA;
   }
   at.nreq = n;
+  // persistent: one CTA per SM, each running every gridDim.x-th tile
+  PA->ntiles = grid;
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+      delete PA;
+      return HS_ECUDA;
+    }
+    grid = std::min(grid, nsm);
+  }
   at.eOp[0] = op_expo[0];
   at.eOp[1] = op_expo[1];
   at.slot = slot_d;
@@ -1484,11 +1500,11 @@ int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGr
   const int depth = tuned_depth(MODE_ATOMS, s, N_L, jobs[0].N_G, n_stage, graph == nullptr, st,
                                 [&](int d) {
                                   PA->n_stage = d;
-                                  return launch_gemm(MODE_ATOMS, s, grid, smem_for(d, stage_bytes),
+                                  return launch_gemm(MODE_ATOMS, s, grid, smem_for(MODE_ATOMS, d, stage_bytes),
                                                      st, *PA);
                                 });
   PA->n_stage = depth;
-  smem = smem_for(depth, stage_bytes);
+  smem = smem_for(MODE_ATOMS, depth, stage_bytes);
   rc = graph ? graph_launch_atoms(*graph, s, grid, smem, st, *PA)
              : launch_gemm(MODE_ATOMS, s, grid, smem, st, *PA);
   delete PA;
@@ -1558,6 +1574,7 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   for (int b = 0; b < nbi; ++b) tiles += 2 * std::min(b + 1, (P.nbj + 1) / 2);  // CTA pairs
   P.nbi = nbi;
   P.band = contract_band();
+  P.ntiles = tiles;  // one tile per CTA
   auto seg = [&](int srcL, int srcR, int nblk) {
     SplitSeg g;
     g.mL = map_of[srcL][0];
@@ -1577,10 +1594,10 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
     const int stage_bytes = 4 * s * TILE_BYTES;
     const int depth = tuned_depth(MODE_CONTRACT, s, N_L, N_G, n_stage, timed, st, [&](int d) {
       P.n_stage = d;
-      return launch_gemm(MODE_CONTRACT, s, tiles, smem_for(d, stage_bytes), st, P);
+      return launch_gemm(MODE_CONTRACT, s, tiles, smem_for(MODE_CONTRACT, d, stage_bytes), st, P);
     });
     P.n_stage = depth;
-    smem = smem_for(depth, stage_bytes);
+    smem = smem_for(MODE_CONTRACT, depth, stage_bytes);
   }
   rc = launch_gemm(MODE_CONTRACT, s, tiles, smem, st, P);
   if (rc == HS_OK && timed && cudaEventRecord(ev[6], st) != cudaSuccess) rc = HS_ECUDA;
