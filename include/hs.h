@@ -71,8 +71,10 @@ enum {
  * the final H/S values are FP64 in every mode). */
 enum {
   HS_FP64 = 0,        /* plain FP64 everywhere */
-  HS_SPLIT_BF16 = 1   /* Ozaki-style slices on BF16 tensor cores (tcgen05), FP32
+  HS_SPLIT_BF16 = 1,  /* Ozaki-style slices on BF16 tensor cores (tcgen05), FP32
                          exact windows, recombined in extended precision to FP64 */
+  HS_REAL = 0x100     /* OR-ed into the precision of hs_plan: the real-symmetric
+                         variant (hs_set_t_real / hs_assemble_real) */
 };
 
 typedef struct {
@@ -92,7 +94,8 @@ typedef struct {
 } hs_info;
 
 /* Create a plan for problems with N_A atoms, N_L = (l_max+1)^2 and N_G <= N_G_max.
- * precision: HS_FP64 or HS_SPLIT_BF16.  slices: 2..7 for split mode (0 = default 5),
+ * precision: HS_FP64 or HS_SPLIT_BF16, OR-ed with HS_REAL for the real-symmetric
+ * variant (below).  slices: 2..7 for split mode (0 = default 5),
  * ignored for FP64.  hbm_budget_bytes: cap on the plan's device workspace plus the
  * H/S outputs of requests in flight (serving admission); 0 = no cap.
  * stream: cudaStream_t to run on (NULL = the legacy default stream).
@@ -146,6 +149,25 @@ int hs_fallback_flags(hs_plan_t plan, int* flags_host);
 
 /* Free the plan and its workspace (waits for requests in flight). */
 int hs_destroy(hs_plan_t plan);
+
+/* ---------------------------------------------------------------------------
+ * Real-symmetric variant.  Sec. 1.1: for systems with inversion symmetry H and S
+ * are real symmetric.  Here A, B are real K x N_G (leading dimension K), T_AA,
+ * T_AB, T_BB real N_A x N_L x N_L blocks (column-major; only the lower triangles of
+ * T_AA and T_BB are read, T^BA = (T^AB)^T), U as above, and H, S real symmetric
+ * N_G x N_G (leading dimension N_G, both triangles written).  All pointers are
+ * DEVICE pointers.  The plan must be created with precision | HS_REAL; such a plan
+ * accepts only these two calls (hs_assemble, hs_assemble_host and hs_set_t return
+ * HS_EINVAL, hs_submit HS_ENOTSUP).  With HS_SPLIT_BF16 every operand is sliced as
+ * a real array (one K position per row, no rotated copy: half the slice bytes and a
+ * quarter of the tensor work of the complex form at equal sizes).  With HS_FP64 the
+ * call embeds A, B as complex and runs the complex FP64 kernels (reference form).
+ * The factorisation embeds T as complex and uses the complex kernels; imaginary
+ * parts stay exactly zero.  Errors and blocking as hs_assemble. */
+int hs_set_t_real(hs_plan_t plan, const double* T_AA, const double* T_AB, const double* T_BB);
+int hs_assemble_real(hs_plan_t plan, const double* A, const double* B, const double* T_AA,
+                     const double* T_AB, const double* T_BB, const double* U, int N_A, int N_L,
+                     int N_G, double* H, double* S, hs_info* info);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free FP64 assembly (a library addition; the paper has no

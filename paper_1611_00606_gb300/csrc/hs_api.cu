@@ -38,15 +38,21 @@ size_t hs_plan_s::ws_bytes(int N_G, int n_fail) const {
   const size_t K = (size_t)N_A * N_L;
   const size_t nf = (size_t)(n_fail > 0 ? n_fail : 1);
   size_t b = 0;
-  b += 2 * 16 * K * (size_t)N_G;            // Z, W2 (= [Y; X])
-  b += 16 * nf * N_L * (size_t)N_G;         // AF (A rows of failing atoms)
+  b += 2 * ws_elem() * K * (size_t)N_G;     // Z, W2 (= [Y; X])
+  b += ws_elem() * nf * N_L * (size_t)N_G;  // AF (A rows of failing atoms)
   b += split_ws_bytes(N_G, n_fail);
   return b;
 }
 
 size_t hs_plan_s::fixed_bytes() const {
-  return (size_t)16 * N_A * N_L * N_L * 3 + (size_t)sizeof(int) * (3 * N_A + 16) +
-         split_fixed_bytes();
+  size_t b = (size_t)16 * N_A * N_L * N_L * 3 + (size_t)sizeof(int) * (3 * N_A + 16) +
+             split_fixed_bytes();
+  if (real) {
+    b += (size_t)16 * N_A * N_L * N_L * 3;  // Tc
+    if (precision == HS_FP64)               // Ac, Bc, Hc, Sc
+      b += (size_t)2 * 16 * N_A * N_L * N_G_max + (size_t)2 * 16 * N_G_max * (size_t)N_G_max;
+  }
+  return b;
 }
 
 static void free_ptr(void*& p) {
@@ -74,8 +80,9 @@ int hs_plan_s::ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st, bool
     return (async ? hs_malloc_async(ptr, bytes, st, hs_serve_pool(this)) : cudaMalloc(ptr, bytes)) ==
            cudaSuccess;
   };
-  bool ok = al((void**)&w.Z, 16 * K * N_G) && al((void**)&w.W2, 16 * K * N_G) &&
-            al((void**)&w.AF, 16 * nf * N_L * N_G);
+  const size_t e = ws_elem();
+  bool ok = al((void**)&w.Z, e * K * N_G) && al((void**)&w.W2, e * K * N_G) &&
+            al((void**)&w.AF, e * nf * N_L * N_G);
   if (ok) ok = split_ws_alloc(w, N_G, (int)nf, st, async) == HS_OK;
   if (!ok) {
     cudaGetLastError();
@@ -106,6 +113,11 @@ void hs_plan_s::release() {
   free_ptr((void*&)slot_d);
   free_ptr((void*&)fail_list_d);
   free_ptr((void*&)err_d);
+  free_ptr((void*&)Tc);
+  free_ptr((void*&)Ac);
+  free_ptr((void*&)Bc);
+  free_ptr((void*&)Hc);
+  free_ptr((void*&)Sc);
   split_plan_release();
   for (auto& p : stage) free_ptr(p);
   for (auto& e : ev)
@@ -120,6 +132,8 @@ extern "C" int hs_plan(hs_plan_t* out, int N_A, int N_L, int N_G_max, int precis
   *out = nullptr;
   if (N_A < 1 || N_L < 1 || N_L > kMaxNL || N_G_max < 1) return HS_EINVAL;
   if ((long long)N_A * N_L > (1LL << 30)) return HS_EINVAL;
+  const bool real = (precision & HS_REAL) != 0;
+  precision &= ~HS_REAL;
   if (precision != HS_FP64 && precision != HS_SPLIT_BF16) return HS_EINVAL;
   if (precision == HS_SPLIT_BF16) {
     if (slices == 0) slices = kDefaultSlices;
@@ -133,6 +147,7 @@ extern "C" int hs_plan(hs_plan_t* out, int N_A, int N_L, int N_G_max, int precis
   p->N_L = N_L;
   p->N_G_max = N_G_max;
   p->precision = precision;
+  p->real = real;
   p->slices = slices;
   p->budget = hbm_budget_bytes;
   p->stream = (cudaStream_t)stream;
@@ -153,6 +168,15 @@ extern "C" int hs_plan(hs_plan_t* out, int N_A, int N_L, int N_G_max, int precis
   ok = ok && alloc((void**)&p->fail_list_d, sizeof(int) * N_A);
   ok = ok && alloc((void**)&p->err_d, sizeof(int) * 16);
   ok = ok && (p->split_plan_alloc() == HS_OK);
+  if (real) {
+    ok = ok && alloc((void**)&p->Tc, (size_t)3 * 16 * N_A * N_L * N_L);
+    if (precision == HS_FP64) {
+      const size_t K = (size_t)N_A * N_L;
+      ok = ok && alloc((void**)&p->Ac, 16 * K * N_G_max) && alloc((void**)&p->Bc, 16 * K * N_G_max);
+      ok = ok && alloc((void**)&p->Hc, (size_t)16 * N_G_max * N_G_max) &&
+           alloc((void**)&p->Sc, (size_t)16 * N_G_max * N_G_max);
+    }
+  }
   for (auto& e : p->ev) ok = ok && (cudaEventCreate(&e) == cudaSuccess);
   if (!ok) {
     cudaGetLastError();
@@ -168,7 +192,7 @@ extern "C" int hs_plan(hs_plan_t* out, int N_A, int N_L, int N_G_max, int precis
 extern "C" size_t hs_footprint(hs_plan_t p, int N_G) {
   if (!p || N_G < 1 || N_G > p->N_G_max) return 0;
   const int nf = p->t_valid ? p->N_f : p->N_A;
-  return p->ws_bytes(N_G, nf) + (size_t)2 * 16 * N_G * (size_t)N_G;
+  return p->ws_bytes(N_G, nf) + (size_t)2 * (p->real ? 8 : 16) * N_G * (size_t)N_G;
 }
 
 int hs_plan_s::factor(const double2* T_AA, const double2* T_AB, const double2* T_BB) {
@@ -206,7 +230,7 @@ int hs_plan_s::factor(const double2* T_AA, const double2* T_AB, const double2* T
 }
 
 extern "C" int hs_set_t(hs_plan_t p, const hs_z* T_AA, const hs_z* T_AB, const hs_z* T_BB) {
-  if (!p || !T_AA || !T_AB || !T_BB) return HS_EINVAL;
+  if (!p || !T_AA || !T_AB || !T_BB || p->real) return HS_EINVAL;
   std::lock_guard<std::mutex> lk(p->mu);
   if (p->serve_busy()) return HS_EBUSY;  // requests in flight use the cached factor
   int rc = p->factor((const double2*)T_AA, (const double2*)T_AB, (const double2*)T_BB);
@@ -247,8 +271,13 @@ int hs_plan_s::enqueue(const double2* A, const double2* B, int ldAB, const doubl
     HS_CUDA_TRY(hs_launch_contract_fp64(sH, H, N_G, N_G, st));
     if (timed) HS_CUDA_TRY(cudaEventRecord(ev[7], st));
   }
-  HS_CUDA_TRY(hs_launch_mirror(S, N_G, N_G, st));
-  HS_CUDA_TRY(hs_launch_mirror(H, N_G, N_G, st));
+  if (real && precision == HS_SPLIT_BF16) {
+    HS_CUDA_TRY(hs_launch_mirror_real((double*)S, N_G, N_G, st));
+    HS_CUDA_TRY(hs_launch_mirror_real((double*)H, N_G, N_G, st));
+  } else {
+    HS_CUDA_TRY(hs_launch_mirror(S, N_G, N_G, st));
+    HS_CUDA_TRY(hs_launch_mirror(H, N_G, N_G, st));
+  }
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[8], st));
   return HS_OK;
 }
@@ -314,6 +343,7 @@ extern "C" int hs_assemble(hs_plan_t p, const hs_z* A, const hs_z* B, const hs_z
                            int N_L, int N_G, hs_z* H, hs_z* S, hs_info* info) {
   int rc = check_args(p, A, B, T_AA, T_AB, T_BB, U, N_A, N_L, N_G, H, S);
   if (rc) return rc;
+  if (p->real) return HS_EINVAL;  // real plans: hs_assemble_real
   std::lock_guard<std::mutex> lk(p->mu);
   bool factored = false;
   if (!p->t_valid || p->tAA != (const void*)T_AA || p->tAB != (const void*)T_AB ||
@@ -341,6 +371,7 @@ extern "C" int hs_assemble_host(hs_plan_t p, const hs_z* A, const hs_z* B, const
                                 int N_L, int N_G, hs_z* H, hs_z* S, hs_info* info) {
   int rc = check_args(p, A, B, T_AA, T_AB, T_BB, U, N_A, N_L, N_G, H, S);
   if (rc) return rc;
+  if (p->real) return HS_EINVAL;  // real plans: hs_assemble_real (device buffers)
   std::lock_guard<std::mutex> lk(p->mu);
   const size_t K = (size_t)N_A * N_L;
   const size_t nT = (size_t)N_A * N_L * N_L;
@@ -383,6 +414,70 @@ extern "C" int hs_assemble_host(hs_plan_t p, const hs_z* A, const hs_z* B, const
   HS_CUDA_TRY(cudaMemcpyAsync(H, dH, (size_t)16 * N_G * N_G, cudaMemcpyDeviceToHost, st));
   HS_CUDA_TRY(cudaMemcpyAsync(S, dS, (size_t)16 * N_G * N_G, cudaMemcpyDeviceToHost, st));
   HS_CUDA_TRY(cudaStreamSynchronize(st));
+  rc = p->check_device_error();
+  if (rc) return rc;
+  p->fill_info(info, factored);
+  return HS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Real-symmetric variant
+
+int hs_plan_s::factor_real(const double* T_AA, const double* T_AB, const double* T_BB) {
+  const size_t n = (size_t)N_A * N_L * N_L;
+  HS_CUDA_TRY(hs_launch_embed(T_AA, Tc, n, stream));
+  HS_CUDA_TRY(hs_launch_embed(T_AB, Tc + n, n, stream));
+  HS_CUDA_TRY(hs_launch_embed(T_BB, Tc + 2 * n, n, stream));
+  int rc = factor(Tc, Tc + n, Tc + 2 * n);
+  if (rc) return rc;
+  tAA = T_AA;  // the cache is keyed by the caller's real arrays
+  tAB = T_AB;
+  tBB = T_BB;
+  return HS_OK;
+}
+
+extern "C" int hs_set_t_real(hs_plan_t p, const double* T_AA, const double* T_AB,
+                             const double* T_BB) {
+  if (!p || !T_AA || !T_AB || !T_BB || !p->real) return HS_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  int rc = p->factor_real(T_AA, T_AB, T_BB);
+  if (rc == HS_OK) p->factor_pending_info = true;
+  return rc;
+}
+
+extern "C" int hs_assemble_real(hs_plan_t p, const double* A, const double* B,
+                                const double* T_AA, const double* T_AB, const double* T_BB,
+                                const double* U, int N_A, int N_L, int N_G, double* H, double* S,
+                                hs_info* info) {
+  int rc = check_args(p, A, B, T_AA, T_AB, T_BB, U, N_A, N_L, N_G, H, S);
+  if (rc) return rc;
+  if (!p->real) return HS_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  bool factored = false;
+  if (!p->t_valid || p->tAA != (const void*)T_AA || p->tAB != (const void*)T_AB ||
+      p->tBB != (const void*)T_BB) {
+    rc = p->factor_real(T_AA, T_AB, T_BB);
+    if (rc) return rc;
+    factored = true;
+  }
+  rc = ensure_sync_ws(p);
+  if (rc) return rc;
+  const int K = N_A * N_L;
+  if (p->precision == HS_SPLIT_BF16) {
+    // native real: the double arrays travel through the double2-typed plumbing
+    rc = p->enqueue((const double2*)A, (const double2*)B, K, U, N_G, (double2*)H, (double2*)S,
+                    p->ws, p->stream, true);
+    if (rc) return rc;
+  } else {
+    // FP64 form: the complex kernels on A, B embedded as complex, then Re(H), Re(S)
+    HS_CUDA_TRY(hs_launch_embed2d(A, K, p->Ac, K, K, N_G, p->stream));
+    HS_CUDA_TRY(hs_launch_embed2d(B, K, p->Bc, K, K, N_G, p->stream));
+    rc = p->enqueue(p->Ac, p->Bc, K, U, N_G, p->Hc, p->Sc, p->ws, p->stream, true);
+    if (rc) return rc;
+    HS_CUDA_TRY(hs_launch_real_part(p->Hc, N_G, H, N_G, N_G, p->stream));
+    HS_CUDA_TRY(hs_launch_real_part(p->Sc, N_G, S, N_G, N_G, p->stream));
+  }
+  HS_CUDA_TRY(cudaStreamSynchronize(p->stream));
   rc = p->check_device_error();
   if (rc) return rc;
   p->fill_info(info, factored);

@@ -55,6 +55,21 @@ cudaError_t hs_launch_contract_fp64(const SegList& segs, double2* C, int N_G, in
 // Upper triangle := conj(lower), Im(diag) := 0.
 cudaError_t hs_launch_mirror(double2* C, int N_G, int ldC, cudaStream_t st);
 
+// ---- real-symmetric variant helpers (k_real.cu) --------------------------------
+// y[i] = (x[i], 0) for i < n.
+cudaError_t hs_launch_embed(const double* x, double2* y, size_t n, cudaStream_t st);
+// y(r, c) = (x(r, c), 0), r < rows, c < cols, column-major.
+cudaError_t hs_launch_embed2d(const double* x, int ldx, double2* y, int ldy, int rows, int cols,
+                              cudaStream_t st);
+// y = Re(x), n x n column-major.
+cudaError_t hs_launch_real_part(const double2* x, int ldx, double* y, int ldy, int n,
+                                cudaStream_t st);
+// Real A_f gather (as hs_launch_gather_af).
+cudaError_t hs_launch_gather_af_real(const double* A, int ldA, const int* fail_list, int N_f,
+                                     int N_L, int N_G, double* AF, cudaStream_t st);
+// Upper triangle := lower triangle.
+cudaError_t hs_launch_mirror_real(double* C, int N_G, int ldC, cudaStream_t st);
+
 // ---- split-precision kernels (k_split.cu) -------------------------------------
 struct SliceSeg {
   // slices of one stacked operand segment: s arrays [rows_pad][kpad] bf16,

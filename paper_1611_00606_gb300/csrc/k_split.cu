@@ -332,7 +332,12 @@ __device__ __forceinline__ double pair_scaled(float hi, float lo, int k) {
 // K segment's tiles come from, which exponents scale the drain, and the
 // epilogue.
 
-enum { MODE_CONTRACT = 0, MODE_ATOMS = 1 };
+// The _R modes are the real-symmetric variant (real A, B, T, U; H, S real symmetric,
+// Sec. 1.1): operands hold one real K position per row, contraction tiles are
+// 128 x 128 real outputs (B rows = 128 columns of R'), operator rows n = L.
+enum { MODE_CONTRACT = 0, MODE_ATOMS = 1, MODE_CONTRACT_R = 2, MODE_ATOMS_R = 3 };
+__host__ __device__ constexpr bool is_contract(int mode) { return (mode & 1) == 0; }
+__host__ __device__ constexpr bool is_real(int mode) { return mode >= 2; }
 
 struct SplitSeg {
   int mL, mR, mRr;  // tensor maps of L', R', R''
@@ -404,7 +409,8 @@ struct TileId {
 template <int MODE>
 __device__ __forceinline__ TileId decode_tile(const SplitParams& P, int tile) {
   TileId t{};
-  if (MODE == MODE_CONTRACT) {
+  constexpr bool R = is_real(MODE);  // column pairs of 2 x 128 real columns, pair c from row 2c
+  if (is_contract(MODE)) {
     // Clusters of two CTAs: column blocks 2c and 2c + 1 of one row block (which
     // share the L' tiles); row block bi holds column pairs c <= bi (c < npr), so
     // only an odd nbj leaves the last pair a block past the matrix (zero slices,
@@ -416,10 +422,10 @@ __device__ __forceinline__ TileId decode_tile(const SplitParams& P, int tile) {
     for (int b0 = 0; b0 < P.nbi; b0 += P.band) {
       const int b1 = min(b0 + P.band, P.nbi);
       int n = 0;
-      for (int r = b0; r < b1; ++r) n += min(r + 1, npr);
+      for (int r = b0; r < b1; ++r) n += min((R ? r / 2 : r) + 1, npr);
       if (p < n) {
         for (c = 0; c < npr; ++c) {
-          const int lo = max(b0, c), cnt = b1 - lo;
+          const int lo = max(b0, R ? 2 * c : c), cnt = b1 - lo;
           if (p < cnt) {
             bi = lo + p;
             break;
@@ -431,7 +437,7 @@ __device__ __forceinline__ TileId decode_tile(const SplitParams& P, int tile) {
       p -= n;
     }
     t.i0 = bi * BM;
-    t.j0 = (2 * c + (int)cluster_rank()) * BNC;
+    t.j0 = (2 * c + (int)cluster_rank()) * (R ? BN : BNC);
     t.nseg = P.nseg;
     t.N_G = P.N_G;
   } else {
@@ -457,35 +463,38 @@ __device__ __forceinline__ TileId decode_tile(const SplitParams& P, int tile) {
 template <int MODE>
 __device__ __forceinline__ SegInfo seg_info(const SplitParams& P, const TileId& t, int sg) {
   SegInfo si;
-  if (MODE == MODE_CONTRACT) {
+  if (is_contract(MODE)) {
+    // complex: B rows 0..63 from R' and 64..127 from R'' (same 64 columns);
+    // real: B rows = 128 consecutive columns of R'
     const SplitSeg& S = P.seg[sg];
     si.mL = &P.maps[S.mL];
     si.mR1 = &P.maps[S.mR];
-    si.mR2 = &P.maps[S.mRr];
+    si.mR2 = &P.maps[is_real(MODE) ? S.mR : S.mRr];
     si.kbL = 0;
     si.rbL = t.i0 >> 6;
     si.plL = 0;
     si.kbR = 0;
     si.rbR1 = t.j0 >> 6;
-    si.rbR2 = t.j0 >> 6;
+    si.rbR2 = (t.j0 >> 6) + (is_real(MODE) ? 1 : 0);
     si.plR = 0;
     si.kblocks = S.kblocks;
     si.eRow = S.eL;
     si.eC0 = S.eR + t.j0;
-    si.eC1 = S.eR + t.j0;
+    si.eC1 = S.eR + t.j0 + (is_real(MODE) ? 64 : 0);
   } else {
     const AtomsArgs& A = P.at;
     const AtomsReq& R = A.rq[t.r];
     si.mL = &P.maps[sg == 0 ? R.mA : R.mB];
     si.mR1 = si.mR2 = &P.maps[A.mOp[t.job]];
-    si.kbL = (2 * t.a * A.N_L) / KB;  // atom a's rows in the packed layout
+    const int pr = is_real(MODE) ? 1 : 2;  // real K positions per row
+    si.kbL = (pr * t.a * A.N_L) / KB;  // atom a's rows in the packed layout
     si.rbL = t.i0 >> 6;
     si.plL = 0;
     si.kbR = sg * (A.P / KB);  // Z operator: A part in [0, P), B part in [P, 2P)
     si.rbR1 = t.n0 >> 6;
     si.rbR2 = (t.n0 >> 6) + 1;
     si.plR = t.a * P.s;
-    si.kblocks = (2 * (t.a + 1) * A.N_L + KB - 1) / KB - si.kbL;
+    si.kblocks = (pr * (t.a + 1) * A.N_L + KB - 1) / KB - si.kbL;
     si.eRow = sg == 0 ? R.eA : R.eB;
     si.eC0 = A.eOp[t.job] + t.a * A.n_pad + t.n0;
     si.eC1 = si.eC0 + 64;
@@ -537,12 +546,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   constexpr int s = S;
   // CTAs per cluster: a contraction pairs two tiles of one row block, each CTA
   // loading half of the shared L' boxes for both (TMA multicast)
-  constexpr int CL = MODE == MODE_CONTRACT ? 2 : 1;
+  constexpr int CL = is_contract(MODE) ? 2 : 1;
   const int NS = P.n_stage;
   const uint32_t a_bytes = (uint32_t)s * 2 * TILE_BYTES;   // s slices x 128 rows
   const uint32_t stage_bytes = 2 * a_bytes;                 // A part + B part
   const uint32_t ring_bytes =
-      MODE == MODE_CONTRACT ? max(NS * stage_bytes, (uint32_t)STAGING_CONTRACT) : NS * stage_bytes;
+      is_contract(MODE) ? max(NS * stage_bytes, (uint32_t)STAGING_CONTRACT) : NS * stage_bytes;
   uint64_t* full = (uint64_t*)(smem + ring_bytes);
   uint64_t* empty = full + NS;
   uint64_t* acc_full = empty + NS;
@@ -762,13 +771,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
       if (!ok || *abort_flag) break;
       // Results: (hi + lo) * 2^(E_row + E_col) in FP64.  Thread = one tile row; pair k
       // of a strip = its TMEM columns 16 cg + 2k and 2k + 1 (lanes 2k, 2k + 1 of eC*).
-      if (MODE == MODE_CONTRACT) {
+      if (is_contract(MODE)) {
         // one tile per CTA: stage (hi, lo) in the idle ring (every stage was consumed by
         // an MMA that completed before the last acc_full), then write the tile with
         // consecutive threads on consecutive output addresses
         float2* stg = (float2*)smem;  // [2 strips][64 cols][128 rows]
         int* s_erow = (int*)(smem + 2 * 64 * 128 * sizeof(float2));
-        int* s_ecol = s_erow + 128;   // [64]
+        int* s_ecol = s_erow + 128;   // [128]: exponent of each TMEM column
         const int r = 32 * q4 + lane;
 #pragma unroll
         for (int c = 0; c < 16; c += 2) {
@@ -780,9 +789,23 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           stg[(1 * 64 + 16 * cg + c + 1) * 128 + r] = make_float2(hb.y, lb.y);
         }
         if (cg == 0) s_erow[r] = eRow;
-        if (q4 == 0 && lane < 16) s_ecol[16 * cg + lane] = eC0;
+        if (q4 == 0 && lane < 16) {
+          s_ecol[16 * cg + lane] = eC0;
+          s_ecol[64 + 16 * cg + lane] = eC1;
+        }
         asm volatile("bar.sync 1, %0;" ::"r"(32 * NUM_DRAIN_WARPS) : "memory");
         const int dt = threadIdx.x - 64;  // 0 .. 32*NUM_DRAIN_WARPS-1
+        if (is_real(MODE)) {  // 128 real columns
+          double* C = (double*)P.C;
+          for (int idx = dt; idx < 128 * 128; idx += 32 * NUM_DRAIN_WARPS) {
+            const int jj = idx >> 7, ii = idx & 127;
+            const int i = T.i0 + ii, j = T.j0 + jj;
+            if (i < P.N_G && j < P.N_G) {
+              const float2 v = stg[jj * 128 + ii];
+              C[i + (size_t)j * P.ldC] = pair_scaled(v.x, v.y, s_erow[ii] + s_ecol[jj]);
+            }
+          }
+        } else
         for (int idx = dt; idx < 64 * 128; idx += 32 * NUM_DRAIN_WARPS) {
           const int jj = idx >> 7, ii = idx & 127;
           const int i = T.i0 + ii, j = T.j0 + jj;
@@ -791,6 +814,32 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
             const float2 re = stg[jj * 128 + ii], im = stg[(64 + jj) * 128 + ii];
             P.C[i + (size_t)j * P.ldC] = make_double2(pair_scaled(re.x, re.y, k),
                                                       pair_scaled(im.x, im.y, k));
+          }
+        }
+      } else if (is_real(MODE)) {
+        // TMEM column c of strip t = output row L = n0 + 64 t + c (real); each thread
+        // writes pairs of consecutive rows
+        const AtomsArgs& A = P.at;
+        const AtomsReq& R = A.rq[T.r];
+        double* out = T.job == 0 ? (double*)R.Z + (size_t)T.a * A.N_L
+                                 : (double*)R.W2 + (size_t)A.slot[T.a] * A.N_L;
+        const int g = row;
+        const int Lb = T.n0 + 16 * cg;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int e00 = eRow + __shfl_sync(0xffffffffu, eC0, 2 * k);
+          const int e01 = eRow + __shfl_sync(0xffffffffu, eC0, 2 * k + 1);
+          const int e10 = eRow + __shfl_sync(0xffffffffu, eC1, 2 * k);
+          const int e11 = eRow + __shfl_sync(0xffffffffu, eC1, 2 * k + 1);
+          const float2 ha = unpack2(h0[k]), la = unpack2(l0[k]);
+          const float2 hb = unpack2(h1[k]), lb = unpack2(l1[k]);
+          const int L0 = Lb + 2 * k, L1 = Lb + 64 + 2 * k;
+          double* o = out + (size_t)g * A.ld;
+          if (g < T.N_G) {
+            if (L0 < A.N_L) o[L0] = pair_scaled(ha.x, la.x, e00);
+            if (L0 + 1 < A.N_L) o[L0 + 1] = pair_scaled(ha.y, la.y, e01);
+            if (L1 < A.N_L) o[L1] = pair_scaled(hb.x, lb.x, e10);
+            if (L1 + 1 < A.N_L) o[L1 + 1] = pair_scaled(hb.y, lb.y, e11);
           }
         }
       } else {
@@ -1058,6 +1107,101 @@ __global__ void __launch_bounds__(128) k_slice_op(const double2* __restrict__ M,
   }
 }
 
+// Real sources (real-symmetric variant): nblk * N_L real rows per column, packed one
+// K position per row (kpad = roundup(K, 16)); a thread writes the pair of positions
+// (2j, 2j + 1) as one 32-bit word per slice, with k_slice's digit and exponent rules
+// (no rotated copy: a real contraction needs none).
+__global__ void __launch_bounds__(256) k_slice_real(const __grid_constant__ SliceParams P) {
+  const SliceJob J = P.job[blockIdx.y];
+  const int g = blockIdx.x;
+  const int s = P.s;
+  const int K = J.nblk * P.N_L;                // real rows of the source
+  const int kpad = ((K + KB - 1) / KB) * KB;   // packed K, whole 16-wide blocks
+  const size_t slice_elems = (size_t)P.rows_pad * kpad;
+  __shared__ unsigned long long red[32];
+  __shared__ int s_E;
+  const int kc = kpad / 2;  // position pairs per row
+  const int NKB = kpad / KB;
+  if (g >= P.N_G) {
+    for (int k = threadIdx.x; k < kc; k += blockDim.x)
+      for (int p = 0; p < s; ++p)
+        *(uint32_t*)(J.plain + p * slice_elems + tile_off(g, k, NKB)) = 0u;
+    if (threadIdx.x == 0) J.expo[g] = 0;
+    return;
+  }
+  const double* col = (const double*)J.X + (size_t)g * J.ldX;
+  unsigned long long m = 0ull;  // bit pattern of the column's largest finite |value| (x |u|)
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double v = col[k];
+    m = max(m, finite_abs_bits(J.u ? v * J.u[k] : v));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long mm = 0ull;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = max(mm, red[i]);
+    s_E = slice_exponent(__longlong_as_double((long long)mm));
+    J.expo[g] = s_E;
+  }
+  __syncthreads();
+  const int E = s_E;
+  for (int j = threadIdx.x; j < kc; j += blockDim.x) {
+    const int k0 = 2 * j, k1 = k0 + 1;
+    double x0 = k0 < K ? col[k0] : 0.0, x1 = k1 < K ? col[k1] : 0.0;
+    if (J.u) {
+      if (k0 < K) x0 *= J.u[k0];
+      if (k1 < K) x1 *= J.u[k1];
+    }
+    put_slices(make_double2(x0, x1), k0 >= K, E, s, J.plain, nullptr, slice_elems,
+               tile_off(g, j, NKB));
+  }
+}
+
+// Real per-atom operators: the real parts of the (embedded) MZ[a] and M2[a]; operator
+// row n = output row L; column l of a part at real position (a N_L) mod 16 + l of the
+// part, zeros elsewhere (the packed real layout's offset of atom a).
+__global__ void __launch_bounds__(128) k_slice_op_real(const double2* __restrict__ M, int job,
+                                                       int N_A, int N_L, int P, int n_pad, int s,
+                                                       uint16_t* __restrict__ out,
+                                                       int* __restrict__ expo) {
+  const int a = blockIdx.y, L = blockIdx.x;  // L < n_pad
+  const int parts = job == 0 ? 2 : 1;
+  const int Kop = parts * P;
+  const size_t slice_elems = (size_t)n_pad * Kop;
+  uint16_t* base = out + (size_t)a * s * slice_elems;
+  const int ldM = N_L;
+  const double2* Ma = M + (size_t)a * N_L * (parts * N_L);
+  __shared__ unsigned long long red[4];
+  __shared__ int s_E;
+  unsigned long long m = 0ull;
+  if (L < N_L)
+    for (int k = threadIdx.x; k < parts * N_L; k += blockDim.x)
+      m = max(m, finite_abs_bits(Ma[L + (size_t)k * ldM].x));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long mm = max(max(red[0], red[1]), max(red[2], red[3]));
+    s_E = slice_exponent(__longlong_as_double((long long)mm));
+    expo[(size_t)a * n_pad + L] = s_E;
+  }
+  __syncthreads();
+  const int E = s_E;
+  const int oa = (a * N_L) & (KB - 1);  // atom a's offset inside its first K block
+  for (int j = threadIdx.x; j < Kop / 2; j += blockDim.x) {
+    double x[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = 2 * j + h;
+      const int part = q / P, l = q - part * P - oa;
+      x[h] = (L < N_L && l >= 0 && l < N_L) ? Ma[L + (size_t)(part * N_L + l) * ldM].x : 0.0;
+    }
+    put_slices(make_double2(x[0], x[1]), L >= N_L, E, s, base, nullptr, slice_elems,
+               tile_off(L, j, Kop / KB));
+  }
+}
+
 // ------------------------------------------------------------------ host side
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -1092,36 +1236,47 @@ bool encode_tiles(CUtensorMap* m, const uint16_t* base, int NKB, int NRB, int pl
 
 }  // namespace
 
-static inline int rows_pad_of(int N_G) { return ((N_G + ROWS_ALIGN - 1) / ROWS_ALIGN) * ROWS_ALIGN; }
-// Packed real K of a source of nblk blocks of N_L complex rows (whole 16-wide blocks).
-static inline int kpad_of(int nblk, int N_L) { return ((2 * nblk * N_L + KB - 1) / KB) * KB; }
+// Rows (operand columns g) of a slice array: whole 128-row blocks; 256 for real plans,
+// whose contraction column pairs span 256 columns.
+static inline int rows_pad_of(int N_G, bool real = false) {
+  const int al = real ? 2 * ROWS_ALIGN : ROWS_ALIGN;
+  return ((N_G + al - 1) / al) * al;
+}
+// Packed real K of a source of nblk blocks of N_L rows (whole 16-wide blocks): two
+// positions per complex row, one per real row.
+static inline int kpad_of(int nblk, int N_L, bool real = false) {
+  return (((real ? 1 : 2) * nblk * N_L + KB - 1) / KB) * KB;
+}
 // Real K of one part of a per-atom operator: the most 16-wide K blocks any atom's
-// rows [2 a N_L, 2 (a+1) N_L) of the packed layout touch.
-static int op_part_k(int N_A, int N_L) {
+// rows [pr a N_L, pr (a+1) N_L) of the packed layout touch (pr positions per row).
+static int op_part_k(int N_A, int N_L, bool real = false) {
+  const int pr = real ? 1 : 2;
   int nkb = 0;
   for (int a = 0; a < N_A; ++a)
-    nkb = std::max(nkb, (2 * (a + 1) * N_L + KB - 1) / KB - (2 * a * N_L) / KB);
+    nkb = std::max(nkb, (pr * (a + 1) * N_L + KB - 1) / KB - (pr * a * N_L) / KB);
   return nkb * KB;
 }
-// Operator rows (2 N_L real rows) padded to whole 128-row MMA tiles.
-static inline int op_rows_pad(int N_L) { return ((2 * N_L + BN - 1) / BN) * BN; }
+// Operator rows (2 N_L real rows; N_L for real plans) padded to whole 128-row tiles.
+static inline int op_rows_pad(int N_L, bool real = false) {
+  return (((real ? 1 : 2) * N_L + BN - 1) / BN) * BN;
+}
 
 // Blocks (of N_L complex rows) of each source and whether it needs the rotated copy.
-static void source_shape(int src, int N_A, int n_fail, int& nblk, bool& rot) {
-  rot = (src != SRC_AF);
+static void source_shape(int src, int N_A, int n_fail, bool real, int& nblk, bool& rot) {
+  rot = !real && (src != SRC_AF);
   nblk = (src == SRC_AF || src == SRC_X) ? n_fail : N_A;
 }
 
 size_t hs_plan_s::split_ws_bytes(int N_G, int n_fail) const {
   if (precision != HS_SPLIT_BF16) return 0;
   const int nf = n_fail > 0 ? n_fail : 1;
-  const int rp = rows_pad_of(N_G);
+  const int rp = rows_pad_of(N_G, real);
   size_t b = 0;
   for (int src = 0; src < NSRC; ++src) {
     int nblk;
     bool rot;
-    source_shape(src, N_A, nf, nblk, rot);
-    const size_t one = (size_t)slices * rp * kpad_of(nblk, N_L) * 2;
+    source_shape(src, N_A, nf, real, nblk, rot);
+    const size_t one = (size_t)slices * rp * kpad_of(nblk, N_L, real) * 2;
     b += (rot ? 2 : 1) * one + sizeof(int) * rp;
   }
   return b;
@@ -1130,7 +1285,7 @@ size_t hs_plan_s::split_ws_bytes(int N_G, int n_fail) const {
 int hs_plan_s::split_ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st, bool async) {
   if (precision != HS_SPLIT_BF16) return HS_OK;
   if (!get_encode()) return HS_ECUDA;
-  const int rp = rows_pad_of(N_G);
+  const int rp = rows_pad_of(N_G, real);
   auto al = [&](void** ptr, size_t bytes) -> bool {
     return (async ? hs_malloc_async(ptr, bytes, st, hs_serve_pool(this)) : cudaMalloc(ptr, bytes)) ==
            cudaSuccess;
@@ -1138,8 +1293,8 @@ int hs_plan_s::split_ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st
   for (int src = 0; src < NSRC; ++src) {
     int nblk;
     bool rot;
-    source_shape(src, N_A, n_fail, nblk, rot);
-    const size_t one = (size_t)slices * rp * kpad_of(nblk, N_L) * 2;
+    source_shape(src, N_A, n_fail, real, nblk, rot);
+    const size_t one = (size_t)slices * rp * kpad_of(nblk, N_L, real) * 2;
     if (!al((void**)&w.sb[src].plain, one)) return HS_ENOMEM;
     if (rot && !al((void**)&w.sb[src].rot, one)) return HS_ENOMEM;
     if (!al((void**)&w.sb[src].expo, sizeof(int) * rp)) return HS_ENOMEM;
@@ -1149,14 +1304,14 @@ int hs_plan_s::split_ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st
 
 size_t hs_plan_s::split_fixed_bytes() const {
   if (precision != HS_SPLIT_BF16) return 0;
-  const size_t P = (size_t)op_part_k(N_A, N_L), np = (size_t)op_rows_pad(N_L);
+  const size_t P = (size_t)op_part_k(N_A, N_L, real), np = (size_t)op_rows_pad(N_L, real);
   return (size_t)N_A * slices * np * (3 * P) * 2 + 2 * sizeof(int) * N_A * np;
 }
 
 int hs_plan_s::split_plan_alloc() {
   if (precision != HS_SPLIT_BF16) return HS_OK;
   if (!get_encode()) return HS_ECUDA;
-  const size_t P = (size_t)op_part_k(N_A, N_L), np = (size_t)op_rows_pad(N_L);
+  const size_t P = (size_t)op_part_k(N_A, N_L, real), np = (size_t)op_rows_pad(N_L, real);
   const size_t zb = (size_t)N_A * slices * np * 2 * P * 2, wb = zb / 2;
   if (cudaMalloc((void**)&op_slices[0], zb) != cudaSuccess ||
       cudaMalloc((void**)&op_slices[1], wb) != cudaSuccess ||
@@ -1180,13 +1335,17 @@ void hs_plan_s::split_plan_release() {
 // Slice MZ and M2 (k-independent) after every factorisation.
 int hs_plan_s::split_factor(cudaStream_t st) {
   if (precision != HS_SPLIT_BF16) return HS_OK;
-  const int P = op_part_k(N_A, N_L), np = op_rows_pad(N_L);
-  k_slice_op<<<dim3(np, N_A), 128, 0, st>>>(MZ, 0, N_A, N_L, P, np, slices, op_slices[0],
-                                             op_expo[0]);
-  HS_CUDA_TRY(cudaGetLastError());
-  k_slice_op<<<dim3(np, N_A), 128, 0, st>>>(M2, 1, N_A, N_L, P, np, slices, op_slices[1],
-                                             op_expo[1]);
-  HS_CUDA_TRY(cudaGetLastError());
+  const int P = op_part_k(N_A, N_L, real), np = op_rows_pad(N_L, real);
+  for (int job = 0; job < 2; ++job) {
+    const double2* M = job == 0 ? MZ : M2;
+    if (real)
+      k_slice_op_real<<<dim3(np, N_A), 128, 0, st>>>(M, job, N_A, N_L, P, np, slices,
+                                                      op_slices[job], op_expo[job]);
+    else
+      k_slice_op<<<dim3(np, N_A), 128, 0, st>>>(M, job, N_A, N_L, P, np, slices, op_slices[job],
+                                                 op_expo[job]);
+    HS_CUDA_TRY(cudaGetLastError());
+  }
   return HS_OK;
 }
 
@@ -1201,7 +1360,7 @@ template <int MODE, int S>
 static int launch_one(int grid, size_t smem, cudaStream_t st, const SplitParams& P) {
   int rc = set_smem((const void*)k_split_gemm<MODE, S>, smem);
   if (rc) return rc;
-  if (MODE == MODE_ATOMS) {
+  if (!is_contract(MODE)) {
     k_split_gemm<MODE, S><<<grid, NUM_THREADS, smem, st>>>(P);
     return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
   }
@@ -1237,21 +1396,28 @@ static int launch_mode(int s, int grid, size_t smem, cudaStream_t st, const Spli
 
 static int launch_gemm(int mode, int s, int grid, size_t smem, cudaStream_t st,
                        const SplitParams& P) {
-  return mode == MODE_CONTRACT ? launch_mode<MODE_CONTRACT>(s, grid, smem, st, P)
-                               : launch_mode<MODE_ATOMS>(s, grid, smem, st, P);
+  switch (mode) {
+    case MODE_CONTRACT: return launch_mode<MODE_CONTRACT>(s, grid, smem, st, P);
+    case MODE_ATOMS: return launch_mode<MODE_ATOMS>(s, grid, smem, st, P);
+    case MODE_CONTRACT_R: return launch_mode<MODE_CONTRACT_R>(s, grid, smem, st, P);
+    case MODE_ATOMS_R: return launch_mode<MODE_ATOMS_R>(s, grid, smem, st, P);
+    default: return HS_EINVAL;
+  }
 }
 
-static const void* atoms_fn(int s) {
+template <int MODE>
+static const void* atoms_fn_m(int s) {
   switch (s) {
-    case 2: return (const void*)k_split_gemm<MODE_ATOMS, 2>;
-    case 3: return (const void*)k_split_gemm<MODE_ATOMS, 3>;
-    case 4: return (const void*)k_split_gemm<MODE_ATOMS, 4>;
-    case 5: return (const void*)k_split_gemm<MODE_ATOMS, 5>;
-    case 6: return (const void*)k_split_gemm<MODE_ATOMS, 6>;
-    case 7: return (const void*)k_split_gemm<MODE_ATOMS, 7>;
+    case 2: return (const void*)k_split_gemm<MODE, 2>;
+    case 3: return (const void*)k_split_gemm<MODE, 3>;
+    case 4: return (const void*)k_split_gemm<MODE, 4>;
+    case 5: return (const void*)k_split_gemm<MODE, 5>;
+    case 6: return (const void*)k_split_gemm<MODE, 6>;
+    case 7: return (const void*)k_split_gemm<MODE, 7>;
     default: return nullptr;
   }
 }
+static const void* atoms_fn(int s) { return atoms_fn_m<MODE_ATOMS>(s); }
 
 // The grouped per-atom launch as the single kernel node of a CUDA graph:
 // captured once per plan, then re-parameterised (cudaGraphExecKernelNodeSetParams:
@@ -1338,7 +1504,7 @@ void tune_store_locked(const std::string& key, int v) {
 
 size_t smem_for(int mode, int n_stage, int stage_bytes) {
   const size_t ring = (size_t)n_stage * stage_bytes;
-  return (mode == MODE_CONTRACT ? std::max(ring, (size_t)STAGING_CONTRACT) : ring) + 1024 + 256;
+  return (is_contract(mode) ? std::max(ring, (size_t)STAGING_CONTRACT) : ring) + 1024 + 256;
 }
 
 // Depth for this launch; `trial(depth)` enqueues the real work with that depth.
@@ -1409,27 +1575,28 @@ static void slice_job(SliceParams& sp, int& nj, Workspace& w, int src, const dou
   sp.job[nj++] = SliceJob{X, u, b.plain, b.rot, b.expo, ldX, nblk};
 }
 
-static int slice_launch(SliceParams& sp, int nj, int s, int N_G, int rp, int N_L,
+static int slice_launch(SliceParams& sp, int nj, int s, int N_G, int rp, int N_L, bool real,
                         cudaStream_t st) {
   sp.s = s;
   sp.N_G = N_G;
   sp.rows_pad = rp;
   sp.N_L = N_L;
-  k_slice<<<dim3(rp, nj), 256, 0, st>>>(sp);
+  if (real) k_slice_real<<<dim3(rp, nj), 256, 0, st>>>(sp);
+  else k_slice<<<dim3(rp, nj), 256, 0, st>>>(sp);
   return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
 }
 
 // 1. slice the inputs A, U.B, B of one k-point
 int hs_plan_s::split_inputs(const double2* A, const double2* B, int ldAB, const double* U,
                             int N_G, Workspace& w, cudaStream_t st) {
-  const int rp = rows_pad_of(N_G);
-  if (rows_pad_of(w.N_G) < rp || w.n_fail < N_f || !w.sb[SRC_A].plain) return HS_EINVAL;
+  const int rp = rows_pad_of(N_G, real);
+  if (rows_pad_of(w.N_G, real) < rp || w.n_fail < N_f || !w.sb[SRC_A].plain) return HS_EINVAL;
   SliceParams sp{};
   int nj = 0;
   slice_job(sp, nj, w, SRC_A, A, ldAB, N_A, nullptr);
   slice_job(sp, nj, w, SRC_UB, B, ldAB, N_A, U);
   slice_job(sp, nj, w, SRC_B, B, ldAB, N_A, nullptr);
-  return slice_launch(sp, nj, slices, N_G, rp, N_L, st);
+  return slice_launch(sp, nj, slices, N_G, rp, N_L, real, st);
 }
 
 // 2. per-atom products of up to kMaxBatch k-points in one grouped launch: Z and
@@ -1437,7 +1604,8 @@ int hs_plan_s::split_inputs(const double2* A, const double2* B, int ldAB, const 
 //    node of the plan's captured graph.
 int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGraph* graph) {
   if (n < 1 || n > kMaxBatch) return HS_EINVAL;
-  const int s = slices, Pp = op_part_k(N_A, N_L), np = op_rows_pad(N_L);
+  const int s = slices, Pp = op_part_k(N_A, N_L, real), np = op_rows_pad(N_L, real);
+  const int mode = real ? MODE_ATOMS_R : MODE_ATOMS;
   int n_stage;
   size_t smem;
   int rc = split_geometry(n_stage, smem);
@@ -1453,11 +1621,11 @@ int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGr
   int grid = 0;
   for (int r = 0; r < n && ok; ++r) {
     Workspace& w = *jobs[r].w;
-    const int rp = rows_pad_of(jobs[r].N_G);
+    const int rp = rows_pad_of(jobs[r].N_G, real);
     AtomsReq& R = at.rq[r];
     R.mA = 2 + 2 * r;
     R.mB = 3 + 2 * r;
-    const int nkb = kpad_of(N_A, N_L) / KB;
+    const int nkb = kpad_of(N_A, N_L, real) / KB;
     ok = encode_tiles(&PA->maps[R.mA], w.sb[SRC_A].plain, nkb, rp / 64, s) &&
          encode_tiles(&PA->maps[R.mB], w.sb[SRC_B].plain, nkb, rp / 64, s);
     R.eA = w.sb[SRC_A].expo;
@@ -1497,16 +1665,16 @@ int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGr
   PA->s = s;
   PA->err = err_d;
   const int stage_bytes = 4 * s * TILE_BYTES;
-  const int depth = tuned_depth(MODE_ATOMS, s, N_L, jobs[0].N_G, n_stage, graph == nullptr, st,
+  const int depth = tuned_depth(mode, s, N_L, jobs[0].N_G, n_stage, graph == nullptr, st,
                                 [&](int d) {
                                   PA->n_stage = d;
-                                  return launch_gemm(MODE_ATOMS, s, grid, smem_for(MODE_ATOMS, d, stage_bytes),
+                                  return launch_gemm(mode, s, grid, smem_for(mode, d, stage_bytes),
                                                      st, *PA);
                                 });
   PA->n_stage = depth;
-  smem = smem_for(MODE_ATOMS, depth, stage_bytes);
+  smem = smem_for(mode, depth, stage_bytes);
   rc = graph ? graph_launch_atoms(*graph, s, grid, smem, st, *PA)
-             : launch_gemm(MODE_ATOMS, s, grid, smem, st, *PA);
+             : launch_gemm(mode, s, grid, smem, st, *PA);
   delete PA;
   return rc;
 }
@@ -1517,12 +1685,17 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   const int K = N_A * N_L;
   const int N_h = N_A - N_f;
   const int s = slices;
-  const int rp = rows_pad_of(N_G);
+  const int rp = rows_pad_of(N_G, real);
+  const int mode = real ? MODE_CONTRACT_R : MODE_CONTRACT;
   int n_stage;
   size_t smem;
   int rc = split_geometry(n_stage, smem);
   if (rc) return rc;
-  HS_CUDA_TRY(hs_launch_gather_af(A, ldAB, fail_list_d, N_f, N_L, N_G, w.AF, st));
+  if (real)
+    HS_CUDA_TRY(hs_launch_gather_af_real((const double*)A, ldAB, fail_list_d, N_f, N_L, N_G,
+                                         (double*)w.AF, st));
+  else
+    HS_CUDA_TRY(hs_launch_gather_af(A, ldAB, fail_list_d, N_f, N_L, N_G, w.AF, st));
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[4], st));
   {
     SliceParams sp{};
@@ -1531,9 +1704,11 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
     if (N_h > 0) slice_job(sp, nj, w, SRC_Y, w.W2, K, N_h, nullptr);
     if (N_f > 0) {
       slice_job(sp, nj, w, SRC_AF, w.AF, N_f * N_L, N_f, nullptr);
-      slice_job(sp, nj, w, SRC_X, w.W2 + (size_t)N_h * N_L, K, N_f, nullptr);
+      const double2* X = real ? (const double2*)((const double*)w.W2 + (size_t)N_h * N_L)
+                              : w.W2 + (size_t)N_h * N_L;
+      slice_job(sp, nj, w, SRC_X, X, K, N_f, nullptr);
     }
-    rc = slice_launch(sp, nj, s, N_G, rp, N_L, st);
+    rc = slice_launch(sp, nj, s, N_G, rp, N_L, real, st);
     if (rc) return rc;
   }
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[5], st));
@@ -1547,10 +1722,13 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   auto add_map = [&](int src, int nblk) -> bool {
     SliceBuf& b = w.sb[src];
     map_of[src][0] = nm;
-    if (!encode_tiles(&P.maps[nm++], b.plain, kpad_of(nblk, N_L) / KB, rp / 64, s)) return false;
+    if (!encode_tiles(&P.maps[nm++], b.plain, kpad_of(nblk, N_L, real) / KB, rp / 64, s))
+      return false;
+    map_of[src][1] = map_of[src][0];  // real plans: no rotated copy
     if (b.rot) {
       map_of[src][1] = nm;
-      if (!encode_tiles(&P.maps[nm++], b.rot, kpad_of(nblk, N_L) / KB, rp / 64, s)) return false;
+      if (!encode_tiles(&P.maps[nm++], b.rot, kpad_of(nblk, N_L, real) / KB, rp / 64, s))
+        return false;
     }
     return true;
   };
@@ -1566,12 +1744,13 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   P.n_stage = n_stage;
   P.N_G = N_G;
   P.ldC = N_G;
-  P.nbj = (N_G + BNC - 1) / BNC;
+  P.nbj = (N_G + (real ? BN : BNC) - 1) / (real ? BN : BNC);  // output column tiles
   P.rows_pad = rp;
   P.err = err_d;
   const int nbi = (N_G + BM - 1) / BM;
   int tiles = 0;
-  for (int b = 0; b < nbi; ++b) tiles += 2 * std::min(b + 1, (P.nbj + 1) / 2);  // CTA pairs
+  for (int b = 0; b < nbi; ++b)  // CTA pairs: column pair c from row block c (2c if real)
+    tiles += 2 * std::min((real ? b / 2 : b) + 1, (P.nbj + 1) / 2);
   P.nbi = nbi;
   P.band = contract_band();
   P.ntiles = tiles;  // one tile per CTA
@@ -1580,7 +1759,7 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
     g.mL = map_of[srcL][0];
     g.mR = map_of[srcR][0];
     g.mRr = map_of[srcR][1];
-    g.kblocks = kpad_of(nblk, N_L) / KB;
+    g.kblocks = kpad_of(nblk, N_L, real) / KB;
     g.eL = w.sb[srcL].expo;
     g.eR = w.sb[srcR].expo;
     return g;
@@ -1592,14 +1771,14 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   P.C = S;
   {
     const int stage_bytes = 4 * s * TILE_BYTES;
-    const int depth = tuned_depth(MODE_CONTRACT, s, N_L, N_G, n_stage, timed, st, [&](int d) {
+    const int depth = tuned_depth(mode, s, N_L, N_G, n_stage, timed, st, [&](int d) {
       P.n_stage = d;
-      return launch_gemm(MODE_CONTRACT, s, tiles, smem_for(MODE_CONTRACT, d, stage_bytes), st, P);
+      return launch_gemm(mode, s, tiles, smem_for(mode, d, stage_bytes), st, P);
     });
     P.n_stage = depth;
-    smem = smem_for(MODE_CONTRACT, depth, stage_bytes);
+    smem = smem_for(mode, depth, stage_bytes);
   }
-  rc = launch_gemm(MODE_CONTRACT, s, tiles, smem, st, P);
+  rc = launch_gemm(mode, s, tiles, smem, st, P);
   if (rc == HS_OK && timed && cudaEventRecord(ev[6], st) != cudaSuccess) rc = HS_ECUDA;
   if (rc == HS_OK) {
     // H = Z^H B + B^H Z + Y^H Y + A_f^H X_f
@@ -1610,7 +1789,7 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
     if (N_f > 0) P.seg[n++] = seg(SRC_AF, SRC_X, N_f);
     P.nseg = n;
     P.C = H;
-    rc = launch_gemm(MODE_CONTRACT, s, tiles, smem, st, P);
+    rc = launch_gemm(mode, s, tiles, smem, st, P);
     if (rc == HS_OK && timed && cudaEventRecord(ev[7], st) != cudaSuccess) rc = HS_ECUDA;
   }
   delete PP;

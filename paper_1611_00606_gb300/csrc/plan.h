@@ -61,6 +61,12 @@ struct hs_plan_s {
   std::mutex mu;
   int device = 0;
   int N_A = 0, N_L = 0, N_G_max = 0, precision = HS_FP64, slices = 0;
+  // HS_REAL plan (real-symmetric variant, hs_assemble_real): T embedded as complex for
+  // the factorisation; the split form is native real (real Z, W2, A_f and slices), the
+  // FP64 form runs the complex kernels on embedded A, B into complex H, S buffers
+  bool real = false;
+  double2* Tc = nullptr;                                          // 3 x N_A x N_L^2
+  double2 *Ac = nullptr, *Bc = nullptr, *Hc = nullptr, *Sc = nullptr;  // FP64 real plans
   size_t budget = 0;
   cudaStream_t stream = nullptr;
 
@@ -104,6 +110,9 @@ struct hs_plan_s {
   int split_factor(cudaStream_t st);
   void release();
   int factor(const double2* T_AA, const double2* T_AB, const double2* T_BB);
+  int factor_real(const double* T_AA, const double* T_AB, const double* T_BB);
+  // bytes of one element of Z, W2, A_f: real doubles for real split plans
+  size_t ws_elem() const { return real && precision == HS_SPLIT_BF16 ? 8 : 16; }
   int enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G, double2* H,
               double2* S, Workspace& w, cudaStream_t st, bool timed);
   int split_enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G,

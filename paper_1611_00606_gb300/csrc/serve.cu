@@ -307,6 +307,7 @@ void hs_plan_s::serve_shutdown() {
 extern "C" int hs_submit(hs_plan_t p, const hs_z* A, const hs_z* B, int ld_AB, const double* U,
                          int N_G, hs_z* H, hs_z* S, int64_t* ticket) {
   if (!p || !A || !B || !U || !H || !S || !ticket || H == S) return HS_EINVAL;
+  if (p->real) return HS_ENOTSUP;  // serving takes complex requests only
   if (N_G < 1 || N_G > p->N_G_max || ld_AB < p->N_A * p->N_L) return HS_EINVAL;
   size_t fp;
   {

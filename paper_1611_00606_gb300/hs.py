@@ -28,7 +28,9 @@ HS_EINVAL, HS_ENOMEM, HS_ECUDA, HS_EBUSY, HS_ETIMEDOUT, HS_EDEVICE, HS_ENOTSUP =
     -1, -2, -3, -4, -5, -6, -7)
 HS_ESCRATCH = -8
 HS_FP64, HS_SPLIT_BF16 = 0, 1
-PRECISIONS = {"fp64": HS_FP64, "split_bf16": HS_SPLIT_BF16}
+HS_REAL = 0x100
+PRECISIONS = {"fp64": HS_FP64, "split_bf16": HS_SPLIT_BF16,
+              "fp64_real": HS_FP64 | HS_REAL, "split_bf16_real": HS_SPLIT_BF16 | HS_REAL}
 
 
 class hs_info(C.Structure):
@@ -58,6 +60,9 @@ SIGNATURES = {
     "hs_destroy": (_I, [_VP]),
     "hs_strerror": (C.c_char_p, [_I]),
     "hs_assemble_static": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _VP, _VP, _VP]),
+    "hs_set_t_real": (_I, [_VP, _VP, _VP, _VP]),
+    "hs_assemble_real": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _VP, _VP,
+                              C.POINTER(hs_info)]),
 }
 
 
@@ -252,6 +257,59 @@ def hs_assemble_static(A, B, T_AA, T_AB, T_BB, U, N_A: int, N_L: int, N_G: int, 
                                    C.c_void_p(stream.cuda_stream)), "hs_assemble_static")
 
 
+# ---------------------------------------------------------------- real-symmetric variant
+
+def _check_real(X, shape, strides, name):
+    import torch
+    if X.dtype != torch.float64 or not X.is_cuda or tuple(X.shape) != shape or \
+            tuple(X.stride()) != strides:
+        raise ValueError(f"{name}: float64 CUDA tensor of shape {shape}, strides {strides}")
+
+
+def to_device_real(X: np.ndarray, device="cuda"):
+    """numpy real (rows, cols) -> column-major float64 CUDA tensor of the same shape."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(X, dtype=np.float64).T)).to(device).T
+
+
+def to_device_T_real(T: np.ndarray, device="cuda"):
+    """numpy real (N_A, N_L, N_L) natural orientation -> column-major-block CUDA tensor."""
+    import torch
+    buf = np.ascontiguousarray(np.swapaxes(np.asarray(T, dtype=np.float64), -1, -2))
+    return torch.from_numpy(buf).to(device).transpose(1, 2)
+
+
+def empty_hs_real(N_G: int, device="cuda"):
+    """Column-major (N_G, N_G) float64 output tensor."""
+    import torch
+    return torch.empty((N_G, N_G), dtype=torch.float64, device=device).T
+
+
+def hs_set_t_real(plan: int, T_AA, T_AB, T_BB) -> None:
+    _check(_lib.hs_set_t_real(plan, _ptr(T_AA), _ptr(T_AB), _ptr(T_BB)), "hs_set_t_real")
+
+
+def hs_assemble_real(plan: int, A, B, T_AA, T_AB, T_BB, U, N_A: int, N_L: int, N_G: int,
+                     H=None, S=None) -> tuple:
+    """Real-symmetric variant (plan made with a *_real precision): real H, S."""
+    K = N_A * N_L
+    _check_real(A, (K, N_G), (1, K), "A")
+    _check_real(B, (K, N_G), (1, K), "B")
+    for T, n in ((T_AA, "T_AA"), (T_AB, "T_AB"), (T_BB, "T_BB")):
+        _check_real(T, (N_A, N_L, N_L), (N_L * N_L, 1, N_L), n)
+    if H is None:
+        H = empty_hs_real(N_G, A.device)
+    if S is None:
+        S = empty_hs_real(N_G, A.device)
+    _check_real(H, (N_G, N_G), (1, N_G), "H")
+    _check_real(S, (N_G, N_G), (1, N_G), "S")
+    info = hs_info()
+    _check(_lib.hs_assemble_real(plan, _ptr(A), _ptr(B), _ptr(T_AA), _ptr(T_AB), _ptr(T_BB),
+                                 _ptr(U), N_A, N_L, N_G, _ptr(H), _ptr(S), C.byref(info)),
+           "hs_assemble_real")
+    return H, S, info.as_dict()
+
+
 def hs_strerror(code: int) -> str:
     return _lib.hs_strerror(code).decode()
 
@@ -267,6 +325,10 @@ class Plan:
     def assemble(self, A, B, T_AA, T_AB, T_BB, U, N_G=None, H=None, S=None):
         N_G = A.shape[1] if N_G is None else N_G
         return hs_assemble(self.h, A, B, T_AA, T_AB, T_BB, U, self.N_A, self.N_L, N_G, H, S)
+
+    def assemble_real(self, A, B, T_AA, T_AB, T_BB, U, N_G=None, H=None, S=None):
+        N_G = A.shape[1] if N_G is None else N_G
+        return hs_assemble_real(self.h, A, B, T_AA, T_AB, T_BB, U, self.N_A, self.N_L, N_G, H, S)
 
     def close(self):
         if self.h:

@@ -20,6 +20,11 @@ Recipe (one tensor id per array, ``numpy.random.Philox(key=(seed, id))``):
 * every Hermitian draw is symmetrised exactly, ``T <- (T + T^H) / 2``;
 * ``U[a, L]``: uniform in [0.5, 2].
 
+Real-symmetric variant (``make_inputs_real``; Sec. 1.1: real H and S for systems
+with inversion symmetry): the same recipe with real normal draws ``N(0, 1)``,
+``T_AA = M M^T + N_L I`` (or shifted), ``T_BB = (N + N^T) / 2``, from streams of
+their own (tensor id + 100).
+
 Indefinite atoms: ``n_f = round(frac * N_A)`` atoms at
 ``(3 + floor(i * N_A / n_f)) mod N_A`` for ``i < n_f``.
 
@@ -157,6 +162,57 @@ def make_inputs(w: Workload, cols: slice | None = None):
     A = coefficients(w.N_A, w.N_L, n, w.seed, _ID_A, col0=c0)
     B = coefficients(w.N_A, w.N_L, n, w.seed, _ID_B, col0=c0)
     T_AA, T_AB, T_BB = t_matrices(w.N_A, w.N_L, w.indefinite, w.seed)
+    U = u_norms(w.N_A, w.N_L, w.seed)
+    return dict(A=A, B=B, T_AA=T_AA, T_AB=T_AB, T_BB=T_BB, U=U)
+
+
+_REAL = 100  # tensor-id offset of the real-variant streams
+
+
+def coefficients_real(N_A: int, N_L: int, N_G: int, seed: int = 0, tid: int = _ID_A,
+                      col0: int = 0, chunk: int = 512) -> np.ndarray:
+    """A real (K, N_G) Fortran-order coefficient matrix, rows scaled as the complex one."""
+    K = N_A * N_L
+    rowscale = np.tile(1.0 / (1.0 + l_of_L(N_L).astype(np.float64)), N_A)
+    out = np.empty((N_G, K), dtype=np.float64)
+    g = 0
+    while g < N_G:
+        gg = col0 + g
+        c = gg // chunk
+        lo = gg - c * chunk
+        n = min(chunk - lo, N_G - g)
+        blk = _rng(seed, tid + _REAL, c).standard_normal(size=(chunk, K))[lo:lo + n]
+        out[g:g + n] = blk * rowscale[None, :]
+        g += n
+    return out.T
+
+
+def t_matrices_real(N_A: int, N_L: int, indefinite=(), seed: int = 0):
+    """Real (T_AA, T_AB, T_BB), each (N_A, N_L, N_L), natural orientation; T_AA, T_BB
+    exactly symmetric."""
+    M = _rng(seed, _ID_TAA + _REAL).standard_normal(size=(N_A, N_L, N_L))
+    T_AA = M @ np.swapaxes(M, -1, -2)
+    eye = np.eye(N_L)
+    T_AA = T_AA + N_L * eye[None]
+    for a in indefinite:
+        T_AA[a] -= 2 * N_L * eye
+    T_AA = 0.5 * (T_AA + np.swapaxes(T_AA, -1, -2))
+    T_AB = _rng(seed, _ID_TAB + _REAL).standard_normal(size=(N_A, N_L, N_L))
+    N = _rng(seed, _ID_TBB + _REAL).standard_normal(size=(N_A, N_L, N_L))
+    T_BB = 0.5 * (N + np.swapaxes(N, -1, -2))
+    return T_AA, T_AB, T_BB
+
+
+def make_inputs_real(w: Workload, cols: slice | None = None):
+    """Real-variant inputs of workload ``w`` (same keys and shapes as make_inputs)."""
+    if cols is None:
+        c0, n = 0, w.N_G
+    else:
+        c0, c1, _ = cols.indices(w.N_G)
+        n = c1 - c0
+    A = coefficients_real(w.N_A, w.N_L, n, w.seed, _ID_A, col0=c0)
+    B = coefficients_real(w.N_A, w.N_L, n, w.seed, _ID_B, col0=c0)
+    T_AA, T_AB, T_BB = t_matrices_real(w.N_A, w.N_L, w.indefinite, w.seed)
     U = u_norms(w.N_A, w.N_L, w.seed)
     return dict(A=A, B=B, T_AA=T_AA, T_AB=T_AB, T_BB=T_BB, U=U)
 

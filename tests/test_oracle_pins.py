@@ -204,3 +204,43 @@ def test_indefinite_recipe_spreads_atoms():
     assert synth.indefinite_atoms(100, 0.05) == (3, 23, 43, 63, 83)
     assert synth.indefinite_atoms(256, 0.02) == (3, 54, 105, 156, 207)
     assert synth.WORKLOADS["tiny"].indefinite == (3,)
+
+
+# ---- real-symmetric variant (Sec. 1.1: real H, S with inversion symmetry)
+
+def _inputs_real(N_A, N_L, N_G, indefinite=(), seed=0):
+    return synth.make_inputs_real(synth.Workload("r", N_A, N_L, N_G, tuple(indefinite), seed))
+
+
+def test_real_inputs_give_real_symmetric_outputs():
+    N_A, N_L, N_G = 3, 9, 40
+    d = _inputs_real(N_A, N_L, N_G, (1,), seed=21)
+    assert d["A"].dtype == np.float64 and np.array_equal(d["T_AA"], np.swapaxes(d["T_AA"], 1, 2))
+    H, S = _run(d, N_A, N_L)
+    assert np.max(np.abs(H.imag)) == 0.0 and np.max(np.abs(S.imag)) == 0.0
+    for X in (H.real, S.real):
+        assert np.linalg.norm(X - X.T) <= 8 * EPS * np.linalg.norm(X)
+
+
+@pytest.mark.parametrize("N_A,N_L,N_G,indef", [(2, 4, 5, (1,)), (3, 4, 8, (0,))])
+def test_real_exact_brute_force(N_A, N_L, N_G, indef):
+    d = _inputs_real(N_A, N_L, N_G, indef, seed=9)
+    H, S = _run(d, N_A, N_L)
+    He, Se = brute.exact_hs(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], N_A, N_L)
+    He, Se = brute.to_complex(He), brute.to_complex(Se)
+    assert np.max(np.abs(He.imag)) == 0.0  # the definition itself is real here
+    Hb, Sb = brute.abs_sum_bound(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], N_A, N_L)
+    n = 4 * N_A * N_L * N_L + 8  # dot-product rounding bound, as for the complex case
+    assert np.all(np.abs(H - He) <= n * EPS * Hb + 1e-300)
+    assert np.all(np.abs(S - Se) <= n * EPS * Sb + 1e-300)
+
+
+def test_real_transposed_tab_enters_as_tba():
+    """With real T, T^BA = (T^AB)^T: H is invariant under swapping (A, B) together with
+    (T^AA, T^BB) and transposing T^AB (the two cross terms trade places)."""
+    N_A, N_L, N_G = 2, 5, 12
+    d = _inputs_real(N_A, N_L, N_G, (), seed=4)
+    H, _ = _run(d, N_A, N_L)
+    H2, _ = assemble(d["B"], d["A"], d["T_BB"], np.swapaxes(d["T_AB"], 1, 2), d["T_AA"], d["U"],
+                     N_A, N_L)
+    assert rel_frobenius(H2, H) <= 16 * EPS
