@@ -21,6 +21,8 @@ independent: weak scaling, no collective on the data path).
 
 ``--impl reference`` times the CPU FP64 oracle on the host cores on a
 bounded column panel of the same workload (the only other use of oracle/).
+``--real`` measures the real-symmetric variant (``hs_assemble_real``) on real
+inputs of the workload's shape, with its own oracle-panel CPU baseline.
 """
 from __future__ import annotations
 
@@ -170,6 +172,84 @@ def run_reference(args, w):
     return 0
 
 
+def run_real(args, w):
+    """Real-symmetric variant (Sec. 1.1): split and FP64 forms of hs_assemble_real on real
+    inputs of the workload's shape; one JSON line (rank 0, one GPU)."""
+    import torch
+    from paper_1611_00606_gb300 import hs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    N_f = len(w.indefinite)
+    F = _flops.assembly_flops(w.N_A, w.N_L, w.N_G, N_f, real=True)
+    d = synth.make_inputs_real(w)
+    A, B = hs.to_device_real(d["A"], dev), hs.to_device_real(d["B"], dev)
+    T = [hs.to_device_T_real(d[k], dev) for k in ("T_AA", "T_AB", "T_BB")]
+    U = hs.to_device_U(d["U"], dev)
+    H, S = hs.empty_hs_real(w.N_G, dev), hs.empty_hs_real(w.N_G, dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for prec, steps in (("split_bf16_real", args.steps), ("fp64_real", args.fp64_steps)):
+        if steps <= 0:
+            continue
+        plan = hs.hs_plan(w.N_A, w.N_L, w.N_G, prec, args.slices if "split" in prec else 0)
+        infos = []
+
+        def one():
+            hs.hs_set_t_real(plan, *T)  # factor every step: no cache across k-points
+            _, _, info = hs.hs_assemble_real(plan, A, B, *T, U, w.N_A, w.N_L, w.N_G, H, S)
+            infos.append(info)
+        for _ in range(max(1, args.warmup if "split" in prec else 1)):
+            one()
+        infos.clear()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            one()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        cols = np.arange(min(256, w.N_G))
+        out[prec] = {"ms_per_step": ms, "tflops": F / ms / 1e9, "kpts_per_s": 1e3 / ms,
+                     "steps": steps,
+                     "phase_ms": {k: round(sum(i[k] for i in infos) / len(infos), 3)
+                                  for k in ("ms_factor", "ms_atoms", "ms_slice", "ms_S", "ms_H",
+                                            "ms_finalize")},
+                     "sample": (H.cpu().numpy()[:, cols], S.cpu().numpy()[:, cols])}
+        hs.hs_destroy(plan)
+    cpu = None
+    if not args.no_cpu_baseline:
+        # CPU baseline leg: the FP64 oracle timed on a 256-column panel of the same
+        # workload; the sampled errors of both GPU forms come from that panel
+        from oracle import assemble, rel_frobenius
+        cols = np.arange(min(256, w.N_G))
+        t0 = time.perf_counter()
+        Hr, Sr = assemble(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], w.N_A, w.N_L,
+                          cols=cols)
+        t = time.perf_counter() - t0
+        cpu = {"value": F * (len(cols) / w.N_G) / t / 1e12, "unit": "TFLOP/s",
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"oracle column panel H[:, :{len(cols)}], S[:, :{len(cols)}] of the real "
+                         f"{w.name} inputs ({t:.1f} s), scaled by N_G/{len(cols)}"}
+        for f in out.values():
+            Hh, Sh = f["sample"]
+            f["max_rel_frobenius_sampled"] = {"H": rel_frobenius(Hh, Hr.real),
+                                              "S": rel_frobenius(Sh, Sr.real),
+                                              "columns": f"0..{cols[-1]}"}
+    for f in out.values():
+        f.pop("sample")
+    sp = out.get("split_bf16_real", {})
+    line = {"metric": "H+S assembly TFLOP/s (real Algorithm 1 flop count) per k-point, "
+                      "real-symmetric variant, split-precision form",
+            "value": sp.get("tflops"), "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sp.get("ms_per_step"),
+            "higher_is_better": True, "dtype": f"bf16 slices x{args.slices}, fp32 windows, fp64 result",
+            "data": "synthetic (real)", "config": {"workload": _wl_desc(w), "variant": "real"},
+            "forms": out, "cpu_baseline": cpu}
+    print(json.dumps(line))
+    return 0
+
+
 def run_serve(args):
     """Serving: Poisson k-point requests through hs_submit / hs_poll (continuous batching).
 
@@ -288,6 +368,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve", action="store_true", help="serving benchmark (hs_submit/hs_poll)")
+    ap.add_argument("--real", action="store_true",
+                    help="real-symmetric variant (hs_assemble_real) on real inputs of the workload")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=0.0, help="Poisson arrivals per s (0: all at t=0)")
     ap.add_argument("--pool", type=int, default=4)
@@ -297,6 +379,8 @@ def main():
     if args.serve:
         return run_serve(args)
     w = synth.WORKLOADS[args.workload]
+    if args.real and args.impl != "reference":
+        return run_real(args, w)
     if args.impl == "reference":
         return run_reference(args, w)
 

@@ -8,14 +8,21 @@ than the listed 2*K*N_G; the Tab. 6 figure is used.
 
 The count is algorithmic and fixed: the library's own lower-triangle fallback
 product, cached Cholesky factors and fused steps do not change it.
+
+Real-symmetric variant (Sec. 1.1): the same steps as real BLAS calls (dgemm, dsymm,
+dsyr2k, dsyrk, dpotrf, dtrmm), each a quarter of its complex count (a complex
+multiply-add is four real ones); the U scaling stays one flop per entry.
 """
 from __future__ import annotations
 
 
-def step_flops(N_A: int, N_L: int, N_G: int, N_f: int) -> dict:
+def step_flops(N_A: int, N_L: int, N_G: int, N_f: int, real: bool = False) -> dict:
     """Per-step flop counts of Algorithm 1 for N_f atoms whose Cholesky fails."""
     K = N_A * N_L
     N_h = N_A - N_f
+    if real:
+        c = step_flops(N_A, N_L, N_G, N_f)
+        return {k: (v if k == "unorm_scaling" else v / 4.0) for k, v in c.items()}
     return {
         "loop1_zgemm": 8.0 * N_A * N_L * N_L * N_G,      # Z_a = T^BA_a A_a
         "loop1_zhemm": 8.0 * N_A * N_L * N_L * N_G,      # Z_a += 1/2 T^BB_a B_a
@@ -31,6 +38,6 @@ def step_flops(N_A: int, N_L: int, N_G: int, N_f: int) -> dict:
     }
 
 
-def assembly_flops(N_A: int, N_L: int, N_G: int, N_f: int) -> float:
+def assembly_flops(N_A: int, N_L: int, N_G: int, N_f: int, real: bool = False) -> float:
     """Total algorithmic flops of one k-point (the TFLOP/s numerator)."""
-    return float(sum(step_flops(N_A, N_L, N_G, N_f).values()))
+    return float(sum(step_flops(N_A, N_L, N_G, N_f, real).values()))
