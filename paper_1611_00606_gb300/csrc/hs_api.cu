@@ -120,6 +120,9 @@ void hs_plan_s::release() {
   free_ptr((void*&)Sc);
   split_plan_release();
   for (auto& p : stage) free_ptr(p);
+  for (auto& e : copy_ev)
+    if (e) { cudaEventDestroy(e); e = nullptr; }
+  if (copy_stream) { cudaStreamDestroy(copy_stream); copy_stream = nullptr; }
   for (auto& e : ev)
     if (e) { cudaEventDestroy(e); e = nullptr; }
 }
@@ -241,13 +244,14 @@ extern "C" int hs_set_t(hs_plan_t p, const hs_z* T_AA, const hs_z* T_AB, const h
 // Enqueue the per-k-point path on stream st using workspace w (the T factor
 // must be current).  ev[3..8] bracket the phases for hs_info when timed.
 int hs_plan_s::enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G,
-                       double2* H, double2* S, Workspace& w, cudaStream_t st, bool timed) {
+                       double2* H, double2* S, Workspace& w, cudaStream_t st, bool timed,
+                       cudaEvent_t s_done, bool presliced) {
   const int K = N_A * N_L;
   const int N_h = N_A - N_f;
   if (w.N_G < N_G || w.n_fail < N_f) return HS_EINVAL;
-  if (timed) HS_CUDA_TRY(cudaEventRecord(ev[3], st));
+  if (timed && !presliced) HS_CUDA_TRY(cudaEventRecord(ev[3], st));
   if (precision == HS_SPLIT_BF16) {
-    int rc = split_enqueue(A, B, ldAB, U, N_G, H, S, w, st, timed);
+    int rc = split_enqueue(A, B, ldAB, U, N_G, H, S, w, st, timed, s_done, presliced);
     if (rc != HS_OK) return rc;
   } else {
     HS_CUDA_TRY(hs_launch_atoms_fp64(MZ, M2, fail_d, slot_d, A, B, ldAB, w.Z, w.W2, K, N_A, N_L,
@@ -267,17 +271,15 @@ int hs_plan_s::enqueue(const double2* A, const double2* B, int ldAB, const doubl
     sH.n = n;
     if (timed) HS_CUDA_TRY(cudaEventRecord(ev[5], st));
     HS_CUDA_TRY(hs_launch_contract_fp64(sS, S, N_G, N_G, st));
+    HS_CUDA_TRY(hs_launch_mirror(S, N_G, N_G, st));  // S final: it can leave while H runs
+    if (s_done) HS_CUDA_TRY(cudaEventRecord(s_done, st));
     if (timed) HS_CUDA_TRY(cudaEventRecord(ev[6], st));
     HS_CUDA_TRY(hs_launch_contract_fp64(sH, H, N_G, N_G, st));
     if (timed) HS_CUDA_TRY(cudaEventRecord(ev[7], st));
   }
-  if (real && precision == HS_SPLIT_BF16) {
-    HS_CUDA_TRY(hs_launch_mirror_real((double*)S, N_G, N_G, st));
-    HS_CUDA_TRY(hs_launch_mirror_real((double*)H, N_G, N_G, st));
-  } else {
-    HS_CUDA_TRY(hs_launch_mirror(S, N_G, N_G, st));
-    HS_CUDA_TRY(hs_launch_mirror(H, N_G, N_G, st));
-  }
+  // (S was mirrored right after its contraction)
+  if (real && precision == HS_SPLIT_BF16) HS_CUDA_TRY(hs_launch_mirror_real((double*)H, N_G, N_G, st));
+  else HS_CUDA_TRY(hs_launch_mirror(H, N_G, N_G, st));
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[8], st));
   return HS_OK;
 }
@@ -390,8 +392,17 @@ extern "C" int hs_assemble_host(hs_plan_t p, const hs_z* A, const hs_z* B, const
   double2* dH = (double2*)p->stage[4];
   double2* dS = (double2*)p->stage[5];
   cudaStream_t st = p->stream;
-  HS_CUDA_TRY(cudaMemcpyAsync(dA, A, 16 * K * N_G, cudaMemcpyHostToDevice, st));
-  HS_CUDA_TRY(cudaMemcpyAsync(dB, B, 16 * K * N_G, cudaMemcpyHostToDevice, st));
+  // Copies run on a copy stream of their own: A and B in column chunks, each sliced
+  // (split form) as soon as it has landed; T first, so the factorisation, whose host
+  // step waits for it, does not wait for A and B; S leaves while H is computed.
+  if (!p->copy_stream) {
+    HS_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+    for (auto& e : p->copy_ev) HS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  cudaStream_t cs = p->copy_stream;
+  constexpr int kChunks = 4;  // copy_ev[0..3]: chunks landed; [4]: start; [5]: S final
+  HS_CUDA_TRY(cudaEventRecord(p->copy_ev[4], st));  // after everything already queued on st
+  HS_CUDA_TRY(cudaStreamWaitEvent(cs, p->copy_ev[4], 0));
   HS_CUDA_TRY(cudaMemcpyAsync(dU, U, 8 * K, cudaMemcpyHostToDevice, st));
   bool factored = false;
   if (!p->t_valid || p->host_tAA != (const void*)T_AA || p->host_tAB != (const void*)T_AB ||
@@ -400,6 +411,21 @@ extern "C" int hs_assemble_host(hs_plan_t p, const hs_z* A, const hs_z* B, const
     HS_CUDA_TRY(cudaMemcpyAsync(dT, T_AA, 16 * nT, cudaMemcpyHostToDevice, st));
     HS_CUDA_TRY(cudaMemcpyAsync(dT + nT, T_AB, 16 * nT, cudaMemcpyHostToDevice, st));
     HS_CUDA_TRY(cudaMemcpyAsync(dT + 2 * nT, T_BB, 16 * nT, cudaMemcpyHostToDevice, st));
+  }
+  int c0[kChunks + 1];
+  for (int c = 0; c <= kChunks; ++c) c0[c] = (int)(((long long)N_G * c / kChunks + 63) / 64 * 64);
+  c0[kChunks] = N_G;
+  for (int c = 0; c < kChunks; ++c) {
+    const size_t off = K * (size_t)std::min(c0[c], N_G);
+    const size_t n = K * (size_t)(std::min(c0[c + 1], N_G) - std::min(c0[c], N_G));
+    if (n) {
+      HS_CUDA_TRY(cudaMemcpyAsync(dA + off, A + off, 16 * n, cudaMemcpyHostToDevice, cs));
+      HS_CUDA_TRY(cudaMemcpyAsync(dB + off, B + off, 16 * n, cudaMemcpyHostToDevice, cs));
+    }
+    HS_CUDA_TRY(cudaEventRecord(p->copy_ev[c], cs));
+  }
+  if (p->host_tAA != (const void*)T_AA || p->host_tAB != (const void*)T_AB ||
+      p->host_tBB != (const void*)T_BB || !p->t_valid) {
     rc = p->factor(dT, dT + nT, dT + 2 * nT);
     if (rc) return rc;
     p->host_tAA = T_AA;
@@ -409,10 +435,28 @@ extern "C" int hs_assemble_host(hs_plan_t p, const hs_z* A, const hs_z* B, const
   }
   rc = ensure_sync_ws(p);
   if (rc) return rc;
-  rc = p->enqueue(dA, dB, (int)K, dU, N_G, dH, dS, p->ws, st, true);
+  const bool split = p->precision == HS_SPLIT_BF16;
+  if (split) {
+    HS_CUDA_TRY(cudaEventRecord(p->ev[3], st));
+    for (int c = 0; c < kChunks; ++c) {
+      HS_CUDA_TRY(cudaStreamWaitEvent(st, p->copy_ev[c], 0));
+      const int g0 = std::min(c0[c], N_G), g1 = std::min(c0[c + 1], N_G);
+      // the last chunk also writes the zero rows past N_G (ng = -1: up to the padding)
+      if (g1 > g0 || c == kChunks - 1) {
+        rc = p->split_inputs(dA, dB, (int)K, dU, N_G, p->ws, st, g0,
+                             c == kChunks - 1 ? -1 : g1 - g0);
+        if (rc) return rc;
+      }
+    }
+  } else {
+    HS_CUDA_TRY(cudaStreamWaitEvent(st, p->copy_ev[kChunks - 1], 0));
+  }
+  rc = p->enqueue(dA, dB, (int)K, dU, N_G, dH, dS, p->ws, st, true, p->copy_ev[5], split);
   if (rc) return rc;
+  HS_CUDA_TRY(cudaStreamWaitEvent(cs, p->copy_ev[5], 0));
+  HS_CUDA_TRY(cudaMemcpyAsync(S, dS, (size_t)16 * N_G * N_G, cudaMemcpyDeviceToHost, cs));
   HS_CUDA_TRY(cudaMemcpyAsync(H, dH, (size_t)16 * N_G * N_G, cudaMemcpyDeviceToHost, st));
-  HS_CUDA_TRY(cudaMemcpyAsync(S, dS, (size_t)16 * N_G * N_G, cudaMemcpyDeviceToHost, st));
+  HS_CUDA_TRY(cudaStreamSynchronize(cs));
   HS_CUDA_TRY(cudaStreamSynchronize(st));
   rc = p->check_device_error();
   if (rc) return rc;

@@ -911,6 +911,7 @@ struct SliceJob {
 struct SliceParams {
   SliceJob job[kMaxJobs];
   int s, N_G, rows_pad, N_L;
+  int g0;  // first operand column of this launch (block x slices column g0 + x)
 };
 
 // Balanced base-512 digits of round(x * 2^(9(s-1) - E)); d[0] is the leading one.
@@ -1004,7 +1005,7 @@ __device__ __forceinline__ void put_slices(double2 v, bool zero, int E, int s, u
 
 __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SliceParams P) {
   const SliceJob J = P.job[blockIdx.y];
-  const int g = blockIdx.x;
+  const int g = P.g0 + blockIdx.x;
   const int s = P.s;
   const int K = J.nblk * P.N_L;                  // complex rows of the source
   const int kpad = ((2 * K + KB - 1) / KB) * KB;  // packed real K, whole 16-wide blocks
@@ -1113,7 +1114,7 @@ __global__ void __launch_bounds__(128) k_slice_op(const double2* __restrict__ M,
 // (no rotated copy: a real contraction needs none).
 __global__ void __launch_bounds__(256) k_slice_real(const __grid_constant__ SliceParams P) {
   const SliceJob J = P.job[blockIdx.y];
-  const int g = blockIdx.x;
+  const int g = P.g0 + blockIdx.x;
   const int s = P.s;
   const int K = J.nblk * P.N_L;                // real rows of the source
   const int kpad = ((K + KB - 1) / KB) * KB;   // packed K, whole 16-wide blocks
@@ -1576,19 +1577,23 @@ static void slice_job(SliceParams& sp, int& nj, Workspace& w, int src, const dou
 }
 
 static int slice_launch(SliceParams& sp, int nj, int s, int N_G, int rp, int N_L, bool real,
-                        cudaStream_t st) {
+                        cudaStream_t st, int g0 = 0, int ng = -1) {
+  if (ng < 0) ng = rp - g0;
+  if (g0 < 0 || ng < 0 || g0 + ng > rp) return HS_EINVAL;
+  if (ng == 0) return HS_OK;  // nothing left to slice
+  sp.g0 = g0;
   sp.s = s;
   sp.N_G = N_G;
   sp.rows_pad = rp;
   sp.N_L = N_L;
-  if (real) k_slice_real<<<dim3(rp, nj), 256, 0, st>>>(sp);
-  else k_slice<<<dim3(rp, nj), 256, 0, st>>>(sp);
+  if (real) k_slice_real<<<dim3(ng, nj), 256, 0, st>>>(sp);
+  else k_slice<<<dim3(ng, nj), 256, 0, st>>>(sp);
   return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
 }
 
 // 1. slice the inputs A, U.B, B of one k-point
 int hs_plan_s::split_inputs(const double2* A, const double2* B, int ldAB, const double* U,
-                            int N_G, Workspace& w, cudaStream_t st) {
+                            int N_G, Workspace& w, cudaStream_t st, int g0, int ng) {
   const int rp = rows_pad_of(N_G, real);
   if (rows_pad_of(w.N_G, real) < rp || w.n_fail < N_f || !w.sb[SRC_A].plain) return HS_EINVAL;
   SliceParams sp{};
@@ -1596,7 +1601,7 @@ int hs_plan_s::split_inputs(const double2* A, const double2* B, int ldAB, const 
   slice_job(sp, nj, w, SRC_A, A, ldAB, N_A, nullptr);
   slice_job(sp, nj, w, SRC_UB, B, ldAB, N_A, U);
   slice_job(sp, nj, w, SRC_B, B, ldAB, N_A, nullptr);
-  return slice_launch(sp, nj, slices, N_G, rp, N_L, real, st);
+  return slice_launch(sp, nj, slices, N_G, rp, N_L, real, st, g0, ng);
 }
 
 // 2. per-atom products of up to kMaxBatch k-points in one grouped launch: Z and
@@ -1681,7 +1686,7 @@ int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGr
 
 // 3. gather A_f, slice the per-atom outputs, and the two stacked contractions
 int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, double2* S,
-                             Workspace& w, cudaStream_t st, bool timed) {
+                             Workspace& w, cudaStream_t st, bool timed, cudaEvent_t s_done) {
   const int K = N_A * N_L;
   const int N_h = N_A - N_f;
   const int s = slices;
@@ -1779,6 +1784,11 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
     smem = smem_for(mode, depth, stage_bytes);
   }
   rc = launch_gemm(mode, s, tiles, smem, st, P);
+  if (rc == HS_OK) {  // S is final once mirrored: it can leave while H is computed
+    const cudaError_t e = real ? hs_launch_mirror_real((double*)S, N_G, N_G, st)
+                               : hs_launch_mirror(S, N_G, N_G, st);
+    if (e != cudaSuccess || (s_done && cudaEventRecord(s_done, st) != cudaSuccess)) rc = HS_ECUDA;
+  }
   if (rc == HS_OK && timed && cudaEventRecord(ev[6], st) != cudaSuccess) rc = HS_ECUDA;
   if (rc == HS_OK) {
     // H = Z^H B + B^H Z + Y^H Y + A_f^H X_f
@@ -1798,12 +1808,12 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
 
 int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const double* U,
                              int N_G, double2* H, double2* S, Workspace& w, cudaStream_t st,
-                             bool timed) {
-  int rc = split_inputs(A, B, ldAB, U, N_G, w, st);
+                             bool timed, cudaEvent_t s_done, bool presliced) {
+  int rc = presliced ? HS_OK : split_inputs(A, B, ldAB, U, N_G, w, st);
   if (rc) return rc;
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[9], st));
   AtomsJob job{&w, N_G};
   rc = split_atoms(&job, 1, st, nullptr);
   if (rc) return rc;
-  return split_outputs(A, ldAB, N_G, H, S, w, st, timed);
+  return split_outputs(A, ldAB, N_G, H, S, w, st, timed, s_done);
 }

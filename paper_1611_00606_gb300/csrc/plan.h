@@ -92,6 +92,9 @@ struct hs_plan_s {
   int* op_expo[2] = {nullptr, nullptr};
 
   int* err_d = nullptr;  // device error word (bounded waits)
+  // hs_assemble_host: copy stream (created on first use) and its events
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_ev[6] = {};
   cudaEvent_t ev[10] = {};
   void* stage[6] = {};   // host-call staging: A, B, T, U, H, S
 
@@ -113,16 +116,23 @@ struct hs_plan_s {
   int factor_real(const double* T_AA, const double* T_AB, const double* T_BB);
   // bytes of one element of Z, W2, A_f: real doubles for real split plans
   size_t ws_elem() const { return real && precision == HS_SPLIT_BF16 ? 8 : 16; }
+  // s_done (optional): recorded on st once S (mirrored) is final, while H is still being
+  // computed; presliced: the split form's inputs were already sliced (split_inputs)
   int enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G, double2* H,
-              double2* S, Workspace& w, cudaStream_t st, bool timed);
+              double2* S, Workspace& w, cudaStream_t st, bool timed, cudaEvent_t s_done = nullptr,
+              bool presliced = false);
   int split_enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G,
-                    double2* H, double2* S, Workspace& w, cudaStream_t st, bool timed);
+                    double2* H, double2* S, Workspace& w, cudaStream_t st, bool timed,
+                    cudaEvent_t s_done = nullptr, bool presliced = false);
   int split_geometry(int& n_stage, size_t& smem) const;
+  // g0, ng: slice only operand columns [g0, g0 + ng) (ng < 0: every column and the zero
+  // rows up to the padded row count)
   int split_inputs(const double2* A, const double2* B, int ldAB, const double* U, int N_G,
-                   Workspace& w, cudaStream_t st);
+                   Workspace& w, cudaStream_t st, int g0 = 0, int ng = -1);
   int split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGraph* graph);
+  // also mirrors S (right after its contraction, then records s_done if given)
   int split_outputs(const double2* A, int ldAB, int N_G, double2* H, double2* S, Workspace& w,
-                    cudaStream_t st, bool timed);
+                    cudaStream_t st, bool timed, cudaEvent_t s_done = nullptr);
   int check_device_error();
   void fill_info(hs_info* info, bool factored);
   bool serve_busy();

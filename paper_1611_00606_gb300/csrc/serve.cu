@@ -162,7 +162,6 @@ void launch_batch(ServeState* S, std::vector<Request*>& batch, std::vector<int>&
     int rr = rc;
     if (rr == HS_OK && cudaStreamWaitEvent(r->st, e_atoms, 0) != cudaSuccess) rr = HS_ECUDA;
     if (rr == HS_OK) rr = p->split_outputs(r->A, r->ld, r->N_G, r->H, r->S, r->ws, r->st, false);
-    if (rr == HS_OK && hs_launch_mirror(r->S, r->N_G, r->N_G, r->st) != cudaSuccess) rr = HS_ECUDA;
     if (rr == HS_OK && hs_launch_mirror(r->H, r->N_G, r->N_G, r->st) != cudaSuccess) rr = HS_ECUDA;
     if (rr == HS_OK) rr = finish_launch(r);
     rcs[i] = rr;
