@@ -123,6 +123,7 @@ void hs_plan_s::release() {
   for (auto& e : copy_ev)
     if (e) { cudaEventDestroy(e); e = nullptr; }
   if (copy_stream) { cudaStreamDestroy(copy_stream); copy_stream = nullptr; }
+  if (s_stream) { cudaStreamDestroy(s_stream); s_stream = nullptr; }
   for (auto& e : ev)
     if (e) { cudaEventDestroy(e); e = nullptr; }
 }
@@ -397,10 +398,12 @@ extern "C" int hs_assemble_host(hs_plan_t p, const hs_z* A, const hs_z* B, const
   // step waits for it, does not wait for A and B; S leaves while H is computed.
   if (!p->copy_stream) {
     HS_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+    HS_CUDA_TRY(cudaStreamCreateWithFlags(&p->s_stream, cudaStreamNonBlocking));
     for (auto& e : p->copy_ev) HS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   cudaStream_t cs = p->copy_stream;
-  constexpr int kChunks = 4;  // copy_ev[0..3]: chunks landed; [4]: start; [5]: S final
+  // copy_ev[0..3]: chunks landed; [4]: start; [5]: S final; [6..9]: chunks sliced
+  constexpr int kChunks = 4;
   HS_CUDA_TRY(cudaEventRecord(p->copy_ev[4], st));  // after everything already queued on st
   HS_CUDA_TRY(cudaStreamWaitEvent(cs, p->copy_ev[4], 0));
   HS_CUDA_TRY(cudaMemcpyAsync(dU, U, 8 * K, cudaMemcpyHostToDevice, st));
@@ -412,8 +415,10 @@ extern "C" int hs_assemble_host(hs_plan_t p, const hs_z* A, const hs_z* B, const
     HS_CUDA_TRY(cudaMemcpyAsync(dT + nT, T_AB, 16 * nT, cudaMemcpyHostToDevice, st));
     HS_CUDA_TRY(cudaMemcpyAsync(dT + 2 * nT, T_BB, 16 * nT, cudaMemcpyHostToDevice, st));
   }
+  // chunk boundaries on 128-column (row-block) multiples; the last chunk ends at N_G
   int c0[kChunks + 1];
-  for (int c = 0; c <= kChunks; ++c) c0[c] = (int)(((long long)N_G * c / kChunks + 63) / 64 * 64);
+  for (int c = 0; c <= kChunks; ++c)
+    c0[c] = (int)(((long long)N_G * c / kChunks + 127) / 128 * 128);
   c0[kChunks] = N_G;
   for (int c = 0; c < kChunks; ++c) {
     const size_t off = K * (size_t)std::min(c0[c], N_G);
@@ -437,7 +442,13 @@ extern "C" int hs_assemble_host(hs_plan_t p, const hs_z* A, const hs_z* B, const
   if (rc) return rc;
   const bool split = p->precision == HS_SPLIT_BF16;
   if (split) {
+    // slice each chunk as it lands; on the S stream, the S tiles of its row blocks (a
+    // lower-triangle tile of row block b reads A, U.B columns below 128 (b + 1) only),
+    // so S fills the time the copies leave and the other kernels fill the S launches'
+    // tails; S is mirrored and copied back as soon as its last chunk is done
+    cudaStream_t ss = p->s_stream;
     HS_CUDA_TRY(cudaEventRecord(p->ev[3], st));
+    const int nbi = (N_G + 127) / 128;
     for (int c = 0; c < kChunks; ++c) {
       HS_CUDA_TRY(cudaStreamWaitEvent(st, p->copy_ev[c], 0));
       const int g0 = std::min(c0[c], N_G), g1 = std::min(c0[c + 1], N_G);
@@ -447,16 +458,25 @@ extern "C" int hs_assemble_host(hs_plan_t p, const hs_z* A, const hs_z* B, const
                              c == kChunks - 1 ? -1 : g1 - g0);
         if (rc) return rc;
       }
+      HS_CUDA_TRY(cudaEventRecord(p->copy_ev[6 + c], st));
+      HS_CUDA_TRY(cudaStreamWaitEvent(ss, p->copy_ev[6 + c], 0));
+      const int b0 = std::min(c0[c], N_G) / 128;
+      const int b1 = c == kChunks - 1 ? nbi : std::min(c0[c + 1], N_G) / 128;
+      rc = p->split_contract_S_rows(N_G, dS, p->ws, ss, b0, b1);
+      if (rc) return rc;
     }
+    HS_CUDA_TRY(hs_launch_mirror(dS, N_G, N_G, ss));
+    HS_CUDA_TRY(cudaEventRecord(p->copy_ev[5], ss));
   } else {
     HS_CUDA_TRY(cudaStreamWaitEvent(st, p->copy_ev[kChunks - 1], 0));
   }
-  rc = p->enqueue(dA, dB, (int)K, dU, N_G, dH, dS, p->ws, st, true, p->copy_ev[5], split);
+  rc = p->enqueue(dA, dB, (int)K, dU, N_G, dH, dS, p->ws, st, true,
+                  split ? nullptr : p->copy_ev[5], split);
   if (rc) return rc;
   HS_CUDA_TRY(cudaStreamWaitEvent(cs, p->copy_ev[5], 0));
   HS_CUDA_TRY(cudaMemcpyAsync(S, dS, (size_t)16 * N_G * N_G, cudaMemcpyDeviceToHost, cs));
   HS_CUDA_TRY(cudaMemcpyAsync(H, dH, (size_t)16 * N_G * N_G, cudaMemcpyDeviceToHost, st));
-  HS_CUDA_TRY(cudaStreamSynchronize(cs));
+  HS_CUDA_TRY(cudaStreamSynchronize(cs));  // (after the S stream, whose S-final event it waited for)
   HS_CUDA_TRY(cudaStreamSynchronize(st));
   rc = p->check_device_error();
   if (rc) return rc;

@@ -377,6 +377,7 @@ struct SplitParams {
   int n_stage;    // pipeline depth
   int N_G, ldC, nbj;
   int nbi, band;   // contraction: 128-row blocks, row blocks per band of the tile order
+  int bi0;         // contraction: first row block of this launch (tiles of rows [bi0, nbi))
   int ntiles;      // tiles of the launch; a CTA runs tiles blockIdx.x, + gridDim.x, ...
   int rows_pad;   // slice p of a coefficient-side array starts at row p * rows_pad
   double2* C;
@@ -419,7 +420,7 @@ __device__ __forceinline__ TileId decode_tile(const SplitParams& P, int tile) {
     // cover a compact block of rows x columns and share their operand tiles in L2.
     const int npr = (P.nbj + 1) >> 1;
     int p = tile >> 1, bi = 0, c = 0;
-    for (int b0 = 0; b0 < P.nbi; b0 += P.band) {
+    for (int b0 = P.bi0; b0 < P.nbi; b0 += P.band) {
       const int b1 = min(b0 + P.band, P.nbi);
       int n = 0;
       for (int r = b0; r < b1; ++r) n += min((R ? r / 2 : r) + 1, npr);
@@ -1686,7 +1687,8 @@ int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGr
 
 // 3. gather A_f, slice the per-atom outputs, and the two stacked contractions
 int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, double2* S,
-                             Workspace& w, cudaStream_t st, bool timed, cudaEvent_t s_done) {
+                             Workspace& w, cudaStream_t st, bool timed, cudaEvent_t s_done,
+                             bool skip_S) {
   const int K = N_A * N_L;
   const int N_h = N_A - N_f;
   const int s = slices;
@@ -1783,8 +1785,8 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
     P.n_stage = depth;
     smem = smem_for(mode, depth, stage_bytes);
   }
-  rc = launch_gemm(mode, s, tiles, smem, st, P);
-  if (rc == HS_OK) {  // S is final once mirrored: it can leave while H is computed
+  if (!skip_S) rc = launch_gemm(mode, s, tiles, smem, st, P);
+  if (rc == HS_OK && !skip_S) {  // S is final once mirrored: it can leave while H is computed
     const cudaError_t e = real ? hs_launch_mirror_real((double*)S, N_G, N_G, st)
                                : hs_launch_mirror(S, N_G, N_G, st);
     if (e != cudaSuccess || (s_done && cudaEventRecord(s_done, st) != cudaSuccess)) rc = HS_ECUDA;
@@ -1806,6 +1808,71 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   return rc;
 }
 
+// The S contraction restricted to the lower-triangle tiles of row blocks [bi0, bi1):
+// they read only A and U.B slice rows below 128 * bi1, so a caller that slices column
+// chunks as they arrive can run them before the later chunks exist.
+int hs_plan_s::split_contract_S_rows(int N_G, double2* S, Workspace& w, cudaStream_t st, int bi0,
+                                     int bi1) {
+  const int s = slices;
+  const int rp = rows_pad_of(N_G, real);
+  const int mode = real ? MODE_CONTRACT_R : MODE_CONTRACT;
+  const int nbi = (N_G + BM - 1) / BM;
+  bi0 = std::max(bi0, 0);
+  bi1 = std::min(bi1, nbi);
+  if (bi1 <= bi0) return HS_OK;
+  int n_stage;
+  size_t smem;
+  int rc = split_geometry(n_stage, smem);
+  if (rc) return rc;
+  SplitParams* PP = new (std::nothrow) SplitParams;
+  if (!PP) return HS_ENOMEM;
+  SplitParams& P = *PP;
+  std::memset(&P, 0, sizeof(P));
+  int map_of[2][2];
+  int nm = 0;
+  bool ok = true;
+  for (int i = 0; i < 2 && ok; ++i) {
+    SliceBuf& b = w.sb[i == 0 ? SRC_A : SRC_UB];
+    map_of[i][0] = map_of[i][1] = nm;
+    ok = encode_tiles(&P.maps[nm++], b.plain, kpad_of(N_A, N_L, real) / KB, rp / 64, s);
+    if (ok && b.rot) {
+      map_of[i][1] = nm;
+      ok = encode_tiles(&P.maps[nm++], b.rot, kpad_of(N_A, N_L, real) / KB, rp / 64, s);
+    }
+  }
+  if (!ok) {
+    delete PP;
+    return HS_ECUDA;
+  }
+  P.s = s;
+  P.N_G = N_G;
+  P.ldC = N_G;
+  P.nbj = (N_G + (real ? BN : BNC) - 1) / (real ? BN : BNC);
+  P.rows_pad = rp;
+  P.err = err_d;
+  int tiles = 0;
+  for (int b = bi0; b < bi1; ++b) tiles += 2 * std::min((real ? b / 2 : b) + 1, (P.nbj + 1) / 2);
+  P.bi0 = bi0;
+  P.nbi = bi1;
+  P.band = contract_band();
+  P.ntiles = tiles;
+  for (int i = 0; i < 2; ++i) {
+    SplitSeg& g = P.seg[i];
+    g.mL = map_of[i][0];
+    g.mR = map_of[i][0];
+    g.mRr = map_of[i][1];
+    g.kblocks = kpad_of(N_A, N_L, real) / KB;
+    g.eL = g.eR = w.sb[i == 0 ? SRC_A : SRC_UB].expo;
+  }
+  P.nseg = 2;
+  P.C = S;
+  const int stage_bytes = 4 * s * TILE_BYTES;
+  P.n_stage = tuned_depth(mode, s, N_L, N_G, n_stage, false, st, [](int) { return HS_OK; });
+  rc = launch_gemm(mode, s, tiles, smem_for(mode, P.n_stage, stage_bytes), st, P);
+  delete PP;
+  return rc;
+}
+
 int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const double* U,
                              int N_G, double2* H, double2* S, Workspace& w, cudaStream_t st,
                              bool timed, cudaEvent_t s_done, bool presliced) {
@@ -1815,5 +1882,5 @@ int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const
   AtomsJob job{&w, N_G};
   rc = split_atoms(&job, 1, st, nullptr);
   if (rc) return rc;
-  return split_outputs(A, ldAB, N_G, H, S, w, st, timed, s_done);
+  return split_outputs(A, ldAB, N_G, H, S, w, st, timed, s_done, presliced);
 }

@@ -92,9 +92,9 @@ struct hs_plan_s {
   int* op_expo[2] = {nullptr, nullptr};
 
   int* err_d = nullptr;  // device error word (bounded waits)
-  // hs_assemble_host: copy stream (created on first use) and its events
-  cudaStream_t copy_stream = nullptr;
-  cudaEvent_t copy_ev[6] = {};
+  // hs_assemble_host: copy stream and S stream (created on first use) and their events
+  cudaStream_t copy_stream = nullptr, s_stream = nullptr;
+  cudaEvent_t copy_ev[10] = {};
   cudaEvent_t ev[10] = {};
   void* stage[6] = {};   // host-call staging: A, B, T, U, H, S
 
@@ -117,7 +117,8 @@ struct hs_plan_s {
   // bytes of one element of Z, W2, A_f: real doubles for real split plans
   size_t ws_elem() const { return real && precision == HS_SPLIT_BF16 ? 8 : 16; }
   // s_done (optional): recorded on st once S (mirrored) is final, while H is still being
-  // computed; presliced: the split form's inputs were already sliced (split_inputs)
+  // computed; presliced (split form): the caller already sliced the inputs and contracted
+  // and mirrored S (the host call's streamed path)
   int enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G, double2* H,
               double2* S, Workspace& w, cudaStream_t st, bool timed, cudaEvent_t s_done = nullptr,
               bool presliced = false);
@@ -130,9 +131,14 @@ struct hs_plan_s {
   int split_inputs(const double2* A, const double2* B, int ldAB, const double* U, int N_G,
                    Workspace& w, cudaStream_t st, int g0 = 0, int ng = -1);
   int split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGraph* graph);
-  // also mirrors S (right after its contraction, then records s_done if given)
+  // also mirrors S (right after its contraction, then records s_done if given);
+  // skip_S: S was already contracted and mirrored by the caller
   int split_outputs(const double2* A, int ldAB, int N_G, double2* H, double2* S, Workspace& w,
-                    cudaStream_t st, bool timed, cudaEvent_t s_done = nullptr);
+                    cudaStream_t st, bool timed, cudaEvent_t s_done = nullptr,
+                    bool skip_S = false);
+  // S contraction tiles of row blocks [bi0, bi1) only (no mirror)
+  int split_contract_S_rows(int N_G, double2* S, Workspace& w, cudaStream_t st, int bi0,
+                            int bi1);
   int check_device_error();
   void fill_info(hs_info* info, bool factored);
   bool serve_busy();
