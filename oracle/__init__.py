@@ -1,4 +1,5 @@
-"""CPU FP64 oracle for FLAPW H/S assembly.
+"""CPU FP64 oracle for FLAPW H/S assembly and the reduction of the generalized
+eigenproblem H c = lambda S c that H and S define.
 
 TEST INFRASTRUCTURE: only tests, the smoke check and the CPU-baseline leg of
 the benchmark may import this package.  It shares no code with the CUDA
@@ -9,3 +10,4 @@ Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 """
 from .hs_oracle import assemble, h_aa, rel_frobenius  # noqa: F401
 from .cholesky import cholesky_lower, fail_flags  # noqa: F401
+from .reduce import reduce_standard, standard_eigenvalues  # noqa: F401

@@ -25,6 +25,12 @@ with inversion symmetry): the same recipe with real normal draws ``N(0, 1)``,
 ``T_AA = M M^T + N_L I`` (or shifted), ``T_BB = (N + N^T) / 2``, from streams of
 their own (tensor id + 100).
 
+Generalized-eigenproblem reduction inputs (``reduce_inputs``; Sec. 1.1: H is
+Hermitian, S Hermitian positive definite): ``S = Q diag(s) Q^H`` with ``Q`` the
+unitary factor of the QR of an ``n x n`` complex normal draw and ``s`` log-spaced
+from ``1/cond`` to 1, ``H = (N + N^H) / 2`` with ``N`` complex normal (tensor ids
+20, 21), both symmetrised exactly.
+
 Indefinite atoms: ``n_f = round(frac * N_A)`` atoms at
 ``(3 + floor(i * N_A / n_f)) mod N_A`` for ``i < n_f``.
 
@@ -46,6 +52,7 @@ import numpy as np
 
 # tensor ids of the counter-based streams
 _ID_A, _ID_B, _ID_TAA, _ID_TAB, _ID_TBB, _ID_U = 1, 2, 3, 4, 5, 6
+_ID_RH, _ID_RS = 20, 21
 
 
 @dataclasses.dataclass(frozen=True)
@@ -215,6 +222,18 @@ def make_inputs_real(w: Workload, cols: slice | None = None):
     T_AA, T_AB, T_BB = t_matrices_real(w.N_A, w.N_L, w.indefinite, w.seed)
     U = u_norms(w.N_A, w.N_L, w.seed)
     return dict(A=A, B=B, T_AA=T_AA, T_AB=T_AB, T_BB=T_BB, U=U)
+
+
+def reduce_inputs(n: int, seed: int = 0, cond: float = 1e3):
+    """(H, S): n x n complex, Fortran order; S Hermitian positive definite with
+    2-norm condition number ``cond`` (up to rounding), H Hermitian."""
+    G = _cnormal(_rng(seed, _ID_RS), (n, n))
+    Q, R = np.linalg.qr(G)
+    Q = Q * (np.diag(R) / np.abs(np.where(np.diag(R) == 0, 1, np.diag(R))))  # unique phase
+    s = np.logspace(-math.log10(cond), 0.0, n) if n > 1 else np.ones(1)
+    S = _herm((Q * s) @ Q.conj().T)
+    H = _herm(_cnormal(_rng(seed, _ID_RH), (n, n)))
+    return np.asfortranarray(H), np.asfortranarray(S)
 
 
 def as_colmajor_T(T: np.ndarray) -> np.ndarray:

@@ -244,3 +244,85 @@ def test_real_transposed_tab_enters_as_tba():
     H2, _ = assemble(d["B"], d["A"], d["T_BB"], np.swapaxes(d["T_AB"], 1, 2), d["T_AA"], d["U"],
                      N_A, N_L)
     assert rel_frobenius(H2, H) <= 16 * EPS
+
+
+# ---------------------------------------------------------------------------
+# Generalized-eigenproblem reduction (Sec. 1.1: H c = lambda S c), oracle/reduce.py
+
+from oracle.reduce import reduce_standard, standard_eigenvalues  # noqa: E402
+
+
+def test_reduce_identity_overlap_is_exact():
+    # S = I: L = I and C = H, exactly
+    H, _ = synth.reduce_inputs(9, seed=3)
+    L, C, fail = reduce_standard(H, np.eye(9, dtype=np.complex128))
+    assert fail == 0
+    assert np.array_equal(L, np.eye(9))
+    assert np.array_equal(C, H)
+
+
+def test_reduce_diagonal_overlap_closed_form():
+    # S = diag(d): L = diag(sqrt d), C_ij = H_ij / sqrt(d_i d_j)
+    d = np.array([1.0, 4.0, 9.0, 0.25, 16.0, 2.25])
+    H, _ = synth.reduce_inputs(6, seed=4)
+    L, C, fail = reduce_standard(H, np.diag(d).astype(np.complex128))
+    assert fail == 0
+    assert np.allclose(L, np.diag(np.sqrt(d)), rtol=0, atol=1e-15)
+    r = np.sqrt(d)
+    assert np.allclose(C, H / np.outer(r, r), rtol=1e-15, atol=1e-15)
+
+
+def test_reduce_2x2_eigenvalues_closed_form():
+    # det(H - lam S) = 0 for 2 x 2: a lam^2 + b lam + c = 0 with a = det S,
+    # b = -(h11 s22 + h22 s11 - 2 Re(h12 conj(s12))), c = det H
+    H = np.array([[2.0, 1.0 - 2.0j], [1.0 + 2.0j, -3.0]])
+    S = np.array([[4.0, 1.0 + 1.0j], [1.0 - 1.0j, 3.0]])
+    a = (S[0, 0] * S[1, 1] - abs(S[0, 1]) ** 2).real
+    b = -(H[0, 0] * S[1, 1] + H[1, 1] * S[0, 0] - 2 * (H[0, 1] * np.conj(S[0, 1])).real).real
+    c = (H[0, 0] * H[1, 1] - abs(H[0, 1]) ** 2).real
+    disc = np.sqrt(b * b - 4 * a * c)
+    lam = np.sort([(-b - disc) / (2 * a), (-b + disc) / (2 * a)])
+    assert np.allclose(standard_eigenvalues(H, S), lam, rtol=1e-14, atol=1e-14)
+
+
+def test_reduce_invariants_fix_l_and_c():
+    # L lower with real positive diagonal and L L^H = S fix L uniquely; L C L^H = H
+    # then fixes C.  A transposed factor, a dropped conjugate or a one-sided
+    # transform breaks one of them.
+    H, S = synth.reduce_inputs(40, seed=5, cond=1e3)
+    L, C, fail = reduce_standard(H, S)
+    assert fail == 0
+    assert np.array_equal(L, np.tril(L))
+    assert np.all(np.diag(L).imag == 0) and np.all(np.diag(L).real > 0)
+    assert rel_frobenius(L @ L.conj().T, S) < 1e-14
+    assert rel_frobenius(L @ C @ L.conj().T, H) < 1e-13
+    assert rel_frobenius(C, C.conj().T) < 1e-14
+
+
+def test_reduce_eigenvalues_match_unsymmetric_route():
+    # eigenvalues of C = those of S^{-1} H, computed by a general (non-Hermitian)
+    # eigensolver that shares no step with the reduction
+    H, S = synth.reduce_inputs(30, seed=6, cond=50.0)
+    ev = np.sort(np.linalg.eigvals(np.linalg.solve(S, H)).real)
+    assert np.allclose(standard_eigenvalues(H, S), ev, rtol=1e-11, atol=1e-11)
+
+
+def test_reduce_factor_matches_textbook_cholesky():
+    H, S = synth.reduce_inputs(25, seed=7)
+    L, _, _ = reduce_standard(H, S)
+    Lt, ok = cholesky_lower(S)
+    assert ok and np.allclose(L, Lt, rtol=0, atol=1e-13)
+
+
+def test_reduce_not_positive_definite_reports_column():
+    # S = L0 L0^H with small integers and L0[2, 2] = 0: the third pivot is exactly 0
+    L0 = np.array([[2, 0, 0, 0], [1, 1, 0, 0], [1, 2, 0, 0], [0, 1, 3, 1]], dtype=np.complex128)
+    S = L0 @ L0.conj().T
+    H = np.eye(4, dtype=np.complex128)
+    assert reduce_standard(H, S)[2] == 3
+    # a negative pivot at column 5, and a NaN at column 2
+    S = np.diag([1.0, 2.0, 3.0, 4.0, -1.0, 6.0]).astype(np.complex128)
+    assert reduce_standard(np.eye(6), S)[2] == 5
+    S = np.eye(3, dtype=np.complex128)
+    S[1, 1] = np.nan
+    assert reduce_standard(np.eye(3), S)[2] == 2
