@@ -23,6 +23,9 @@ independent: weak scaling, no collective on the data path).
 bounded column panel of the same workload (the only other use of oracle/).
 ``--real`` measures the real-symmetric variant (``hs_assemble_real``) on real
 inputs of the workload's shape, with its own oracle-panel CPU baseline.
+``--reduce`` measures the generalized-eigenproblem reduction (``hs_reduce``,
+S = L L^H and C = L^-1 H L^-H) on the H, S the split assembly produces for the
+workload, with the FP64 oracle's time for the same reduction as CPU baseline.
 """
 from __future__ import annotations
 
@@ -250,6 +253,80 @@ def run_real(args, w):
     return 0
 
 
+def run_reduce(args, w):
+    """Generalized-eigenproblem reduction (Sec. 1.1) of the workload's H, S; one JSON
+    line (one GPU).  Each step restores H, S from device copies (outside the timed
+    calls) and runs hs_reduce; the device time is the library's CUDA events."""
+    import torch
+    from paper_1611_00606_gb300 import hs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = w.N_G
+    d = synth.make_inputs(w)
+    A, B = hs.to_device_coef(d["A"], dev), hs.to_device_coef(d["B"], dev)
+    T = [hs.to_device_T(d[k], dev) for k in ("T_AA", "T_AB", "T_BB")]
+    U = hs.to_device_U(d["U"], dev)
+    del d
+    plan = hs.hs_plan(w.N_A, w.N_L, n, "split_bf16", args.slices)
+    H0, S0, _ = hs.hs_assemble(plan, A, B, *T, U, w.N_A, w.N_L, n)
+    del A, B
+    H, S = hs.empty_hs(n, dev), hs.empty_hs(n, dev)
+    Fp = _flops.reduce_flops(n)
+    F = sum(Fp.values())
+
+    def one():
+        H.copy_(H0)
+        S.copy_(S0)
+        return hs.hs_reduce(plan, H, S, n)
+    for _ in range(max(1, args.warmup)):
+        one()
+    torch.cuda.synchronize()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    infos = [one() for _ in range(args.steps)]
+    clocks = clk.stop()
+    ms = sum(i["ms_total"] for i in infos) / len(infos)
+    phase = {k: sum(i[k] for i in infos) / len(infos)
+             for k in ("ms_cholesky", "ms_inverse", "ms_p", "ms_g")}
+    # per step: Cholesky 3 nblk - 1 (diagonal blocks, panels, trailing updates, zeroing),
+    # inverse 2 nblk (identity, diagonal blocks, updates), P, G, G + G^H
+    launches = 5 * ((n + 63) // 64) + 2
+    cpu, err = None, None
+    if not args.no_cpu_baseline:
+        # CPU baseline leg: the FP64 oracle's reduction of the same H, S (whole problem)
+        from oracle import rel_frobenius
+        from oracle.reduce import reduce_standard
+        Hh, Sh = H0.cpu().numpy(), S0.cpu().numpy()
+        t0 = time.perf_counter()
+        Lr, Cr, _ = reduce_standard(Hh, Sh)
+        t = time.perf_counter() - t0
+        cpu = {"value": F / t / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"the whole reduction of {w.name}'s H, S (N_G = {n}) by the oracle "
+                         f"(numpy Cholesky + two triangular solves), {t:.1f} s; same flop count"}
+        err = {"L": rel_frobenius(S.cpu().numpy(), Lr), "C": rel_frobenius(H.cpu().numpy(), Cr)}
+    hs.hs_destroy(plan)
+    gemm_g = Fp["g"] / (phase["ms_g"] / 1e3) / 1e12
+    line = {"metric": "generalized-eigenproblem reduction TFLOP/s (S = L L^H, C = L^-1 H L^-H; "
+                      "20/3 N_G^3 executed flops) per k-point",
+            "value": F / ms / 1e9, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{_wl_desc(w)}: H, S from the split assembly",
+                       "l2": "H, S 0.26 GB each (> L2), restored before each step"},
+            "lapack_equivalent_tflops": _flops.reduce_flops_lapack(n) / ms / 1e9,
+            "phase_ms": {k: round(v, 3) for k, v in phase.items()},
+            "roofline": {"bound": "alu", "kernel": "k_zgemm (G = P W^H)", "achieved": gemm_g,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": gemm_g / FP64_PEAK_TFLOPS, "traffic": None,
+                         "work": "8/3 N_G^3 flops of G = P W^H (FP64 DFMA)",
+                         "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz",
+                         "step_frac": (F / ms / 1e9) / FP64_PEAK_TFLOPS},
+            "cpu_baseline": cpu, "rel_frobenius_vs_oracle": err, "gpu_launches": launches * args.steps,
+            "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
 def run_serve(args):
     """Serving: Poisson k-point requests through hs_submit / hs_poll (continuous batching).
 
@@ -368,6 +445,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve", action="store_true", help="serving benchmark (hs_submit/hs_poll)")
+    ap.add_argument("--reduce", action="store_true",
+                    help="generalized-eigenproblem reduction (hs_reduce) of the workload's H, S")
     ap.add_argument("--real", action="store_true",
                     help="real-symmetric variant (hs_assemble_real) on real inputs of the workload")
     ap.add_argument("--requests", type=int, default=200)
@@ -381,6 +460,8 @@ def main():
     w = synth.WORKLOADS[args.workload]
     if args.real and args.impl != "reference":
         return run_real(args, w)
+    if args.reduce and args.impl != "reference":
+        return run_reduce(args, w)
     if args.impl == "reference":
         return run_reference(args, w)
 

@@ -64,7 +64,8 @@ enum {
   HS_ETIMEDOUT = -5,   /* hs_poll: timeout expired before completion */
   HS_EDEVICE = -6,     /* a kernel set the device error word (bounded wait expired) */
   HS_ENOTSUP = -7,     /* feature not available for this plan */
-  HS_ESCRATCH = -8     /* hs_assemble_static: problem larger than its static scratch */
+  HS_ESCRATCH = -8,    /* hs_assemble_static: problem larger than its static scratch */
+  HS_ENOTPD = -9       /* hs_reduce: S is not positive definite */
 };
 
 /* Arithmetic of the big stacked contractions (the per-atom Cholesky and
@@ -196,6 +197,36 @@ int hs_assemble_real(hs_plan_t plan, const double* A, const double* B, const dou
 int hs_assemble_static(const hs_z* A, const hs_z* B, const hs_z* T_AA, const hs_z* T_AB,
                        const hs_z* T_BB, const double* U, int N_A, int N_L, int N_G,
                        hs_z* H, hs_z* S, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Reduction of the generalized eigenproblem to standard form.  Sec. 1.1: the H and
+ * S of one k-point define the generalized eigenvalue problem
+ *   sum_G' [H_GG' - lambda S_GG'] c_G' = 0,
+ * with S (an overlap) Hermitian positive definite.  hs_reduce computes, in place,
+ *   S <- L        the Cholesky factor, S = L L^H: L lower triangular with a real
+ *                 positive diagonal; the strict upper triangle is set to zero;
+ *   H <- C        C = L^{-1} H L^{-H}, Hermitian (both triangles written, diagonal
+ *                 exactly real); C y = lambda y has the eigenvalues of the pair and
+ *                 c = L^{-H} y.
+ * H and S are DEVICE pointers, N_G x N_G column-major with leading dimension N_G
+ * (the layout hs_assemble writes).  Only the lower triangles are read (H's
+ * diagonal as its real part).  FP64 in every plan precision (the kernels are
+ * bound by the FP64 pipe: 20/3 N_G^3 real flops).  Complex plans only (real plans:
+ * HS_EINVAL).  0 <= N_G <= N_G_max.  The plan allocates 32 N_G^2 bytes of device
+ * workspace on first use (grown on demand, freed by hs_destroy); HS_ENOMEM if that
+ * fails.  Runs on the plan's stream and returns when done.
+ * HS_ENOTPD: a Cholesky pivot of S is zero, negative or NaN; info->fail_col is that
+ * column (1-based), H is unchanged and S holds a partial factor.
+ * info may be NULL. */
+typedef struct {
+  int fail_col;          /* 0, or the failing column of the Cholesky (1-based) */
+  double ms_total;       /* device time of the call (CUDA events) */
+  double ms_cholesky;    /* S = L L^H */
+  double ms_inverse;     /* W = L^{-1} */
+  double ms_p;           /* P = W tril_h(H) (tril_h: lower triangle, diagonal halved) */
+  double ms_g;           /* G = P W^H and C = G + G^H */
+} hs_reduce_info;
+int hs_reduce(hs_plan_t plan, hs_z* H, hs_z* S, int N_G, hs_reduce_info* info);
 
 /* Static description of an error code. */
 const char* hs_strerror(int code);

@@ -27,6 +27,7 @@ extern "C" const char* hs_strerror(int code) {
     case HS_EDEVICE: return "device error word set (bounded wait expired)";
     case HS_ENOTSUP: return "not supported by this plan";
     case HS_ESCRATCH: return "problem larger than the static scratch of hs_assemble_static";
+    case HS_ENOTPD: return "S is not positive definite";
     default: return "unknown error";
   }
 }
@@ -120,6 +121,12 @@ void hs_plan_s::release() {
   free_ptr((void*&)Sc);
   split_plan_release();
   for (auto& p : stage) free_ptr(p);
+  free_ptr((void*&)red_W);
+  free_ptr((void*&)red_P);
+  free_ptr((void*&)red_fail);
+  red_cap = 0;
+  for (auto& e : red_ev)
+    if (e) { cudaEventDestroy(e); e = nullptr; }
   for (auto& e : copy_ev)
     if (e) { cudaEventDestroy(e); e = nullptr; }
   if (copy_stream) { cudaStreamDestroy(copy_stream); copy_stream = nullptr; }
@@ -566,4 +573,71 @@ extern "C" int hs_destroy(hs_plan_t p) {
   }
   delete p;
   return HS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Generalized-eigenproblem reduction (Sec. 1.1): S <- L, H <- L^{-1} H L^{-H}.
+
+extern "C" int hs_reduce(hs_plan_t p, hs_z* H, hs_z* S, int N_G, hs_reduce_info* info) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!p || !H || !S || N_G < 0 || N_G > p->N_G_max || p->real) return HS_EINVAL;
+  if (N_G == 0) return HS_OK;
+  if (H == S) return HS_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  if (p->red_cap < N_G) {
+    free_ptr((void*&)p->red_W);
+    free_ptr((void*&)p->red_P);
+    p->red_cap = 0;
+    const size_t bytes = (size_t)16 * N_G * N_G;
+    if (cudaMalloc((void**)&p->red_W, bytes) != cudaSuccess ||
+        cudaMalloc((void**)&p->red_P, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      free_ptr((void*&)p->red_W);
+      free_ptr((void*&)p->red_P);
+      return HS_ENOMEM;
+    }
+    p->red_cap = N_G;
+  }
+  if (!p->red_fail) {
+    if (cudaMalloc((void**)&p->red_fail, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return HS_ENOMEM;
+    }
+  }
+  for (auto& e : p->red_ev)
+    if (!e) HS_CUDA_TRY(cudaEventCreate(&e));
+  cudaStream_t st = p->stream;
+  double2* dH = (double2*)H;
+  double2* dS = (double2*)S;
+  HS_CUDA_TRY(cudaMemsetAsync(p->red_fail, 0, sizeof(int), st));
+  HS_CUDA_TRY(cudaEventRecord(p->red_ev[0], st));
+  HS_CUDA_TRY(hs_launch_cholesky(dS, N_G, p->red_fail, st));
+  HS_CUDA_TRY(cudaEventRecord(p->red_ev[1], st));
+  HS_CUDA_TRY(hs_launch_tri_inverse(dS, p->red_W, N_G, p->red_fail, st));
+  HS_CUDA_TRY(cudaEventRecord(p->red_ev[2], st));
+  HS_CUDA_TRY(hs_launch_reduce_p(p->red_W, dH, p->red_P, N_G, p->red_fail, st));
+  HS_CUDA_TRY(cudaEventRecord(p->red_ev[3], st));
+  HS_CUDA_TRY(hs_launch_reduce_g(p->red_P, p->red_W, dH, N_G, p->red_fail, st));
+  HS_CUDA_TRY(hs_launch_hermsum(dH, N_G, p->red_fail, st));
+  HS_CUDA_TRY(cudaEventRecord(p->red_ev[4], st));
+  int fail = 0;
+  HS_CUDA_TRY(cudaMemcpyAsync(&fail, p->red_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (info) {
+    auto el = [&](int a, int b) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p->red_ev[a], p->red_ev[b]) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.0;
+      }
+      return (double)ms;
+    };
+    info->fail_col = fail;
+    info->ms_cholesky = el(0, 1);
+    info->ms_inverse = el(1, 2);
+    info->ms_p = el(2, 3);
+    info->ms_g = el(3, 4);
+    info->ms_total = el(0, 4);
+  }
+  return fail ? HS_ENOTPD : HS_OK;
 }

@@ -55,6 +55,23 @@ cudaError_t hs_launch_contract_fp64(const SegList& segs, double2* C, int N_G, in
 // Upper triangle := conj(lower), Im(diag) := 0.
 cudaError_t hs_launch_mirror(double2* C, int N_G, int ldC, cudaStream_t st);
 
+// ---- generalized-eigenproblem reduction (k_reduce.cu) --------------------------
+// All n x n column-major with leading dimension n; *fail is the failure word (0 =
+// positive definite so far); every kernel does nothing once it is set.
+// S <- L (Cholesky, strict upper zeroed); *fail = failing column (1-based).
+cudaError_t hs_launch_cholesky(double2* S, int n, int* fail, cudaStream_t st);
+// W <- L^{-1}.
+cudaError_t hs_launch_tri_inverse(const double2* L, double2* W, int n, const int* fail,
+                                  cudaStream_t st);
+// P <- W tril_h(H) (lower triangle of H, diagonal halved).
+cudaError_t hs_launch_reduce_p(const double2* W, const double2* H, double2* P, int n,
+                               const int* fail, cudaStream_t st);
+// H <- P W^H (full).
+cudaError_t hs_launch_reduce_g(const double2* P, const double2* W, double2* H, int n,
+                               const int* fail, cudaStream_t st);
+// H <- H + H^H (diagonal exactly real).
+cudaError_t hs_launch_hermsum(double2* H, int n, const int* fail, cudaStream_t st);
+
 // ---- real-symmetric variant helpers (k_real.cu) --------------------------------
 // y[i] = (x[i], 0) for i < n.
 cudaError_t hs_launch_embed(const double* x, double2* y, size_t n, cudaStream_t st);

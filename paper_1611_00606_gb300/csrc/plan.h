@@ -97,6 +97,11 @@ struct hs_plan_s {
   cudaEvent_t copy_ev[10] = {};
   cudaEvent_t ev[10] = {};
   void* stage[6] = {};   // host-call staging: A, B, T, U, H, S
+  // hs_reduce: W = L^{-1} and P (n x n each, n = red_cap), failure word, events
+  double2 *red_W = nullptr, *red_P = nullptr;
+  int red_cap = 0;
+  int* red_fail = nullptr;
+  cudaEvent_t red_ev[5] = {};
 
   ServeState* serve = nullptr;
 

@@ -41,3 +41,19 @@ def step_flops(N_A: int, N_L: int, N_G: int, N_f: int, real: bool = False) -> di
 def assembly_flops(N_A: int, N_L: int, N_G: int, N_f: int, real: bool = False) -> float:
     """Total algorithmic flops of one k-point (the TFLOP/s numerator)."""
     return float(sum(step_flops(N_A, N_L, N_G, N_f, real).values()))
+
+
+def reduce_flops(N_G: int) -> dict:
+    """Real flops of the generalized-eigenproblem reduction (hs_reduce) as executed:
+    Cholesky of S, inverse of its factor, P = L^{-1} tril_h(H) and G = P L^{-H}, each
+    a triangle-skipping complex product (a complex multiply-add is 8 real flops):
+    N^3/6, N^3/6, N^3/6 and N^3/3 multiply-adds.  LAPACK's zpotrf + zhegst reach the
+    same result with 4/3 + 4 = 16/3 N^3 (``reduce_flops_lapack``)."""
+    n3 = float(N_G) ** 3
+    return {"cholesky": 4.0 / 3.0 * n3, "inverse": 4.0 / 3.0 * n3, "p": 4.0 / 3.0 * n3,
+            "g": 8.0 / 3.0 * n3}
+
+
+def reduce_flops_lapack(N_G: int) -> float:
+    """zpotrf + zhegst flop count of the same reduction (for comparison)."""
+    return 16.0 / 3.0 * float(N_G) ** 3

@@ -27,6 +27,7 @@ HS_OK, HS_PENDING = 0, 1
 HS_EINVAL, HS_ENOMEM, HS_ECUDA, HS_EBUSY, HS_ETIMEDOUT, HS_EDEVICE, HS_ENOTSUP = (
     -1, -2, -3, -4, -5, -6, -7)
 HS_ESCRATCH = -8
+HS_ENOTPD = -9
 HS_FP64, HS_SPLIT_BF16 = 0, 1
 HS_REAL = 0x100
 PRECISIONS = {"fp64": HS_FP64, "split_bf16": HS_SPLIT_BF16,
@@ -39,6 +40,14 @@ class hs_info(C.Structure):
                 ("ms_S", C.c_double), ("ms_H", C.c_double), ("ms_finalize", C.c_double),
                 ("ms_queue", C.c_double), ("ms_latency", C.c_double),
                 ("inflight_bytes", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hs_reduce_info(C.Structure):
+    _fields_ = [("fail_col", C.c_int), ("ms_total", C.c_double), ("ms_cholesky", C.c_double),
+                ("ms_inverse", C.c_double), ("ms_p", C.c_double), ("ms_g", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -63,6 +72,7 @@ SIGNATURES = {
     "hs_set_t_real": (_I, [_VP, _VP, _VP, _VP]),
     "hs_assemble_real": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _VP, _VP,
                               C.POINTER(hs_info)]),
+    "hs_reduce": (_I, [_VP, _VP, _VP, _I, C.POINTER(hs_reduce_info)]),
 }
 
 
@@ -310,6 +320,23 @@ def hs_assemble_real(plan: int, A, B, T_AA, T_AB, T_BB, U, N_A: int, N_L: int, N
     return H, S, info.as_dict()
 
 
+def hs_reduce(plan: int, H, S, N_G: int = None) -> dict:
+    """Generalized-eigenproblem reduction in place: S <- L (S = L L^H), H <- L^-1 H L^-H.
+    H, S: (N_G, N_G) column-major complex128 CUDA tensors.  Returns the info dict;
+    raises HSError (code HS_ENOTPD, ``fail_col`` attribute) when S is not positive
+    definite."""
+    N_G = H.shape[0] if N_G is None else N_G
+    _check_out(H, N_G, "H")
+    _check_out(S, N_G, "S")
+    info = hs_reduce_info()
+    rc = _lib.hs_reduce(plan, _ptr(H), _ptr(S), N_G, C.byref(info))
+    if rc < 0:
+        err = HSError(rc, "hs_reduce")
+        err.fail_col = info.fail_col
+        raise err
+    return info.as_dict()
+
+
 def hs_strerror(code: int) -> str:
     return _lib.hs_strerror(code).decode()
 
@@ -329,6 +356,9 @@ class Plan:
     def assemble_real(self, A, B, T_AA, T_AB, T_BB, U, N_G=None, H=None, S=None):
         N_G = A.shape[1] if N_G is None else N_G
         return hs_assemble_real(self.h, A, B, T_AA, T_AB, T_BB, U, self.N_A, self.N_L, N_G, H, S)
+
+    def reduce(self, H, S, N_G=None):
+        return hs_reduce(self.h, H, S, N_G)
 
     def close(self):
         if self.h:

@@ -1,0 +1,165 @@
+"""Parity of hs_reduce (generalized-eigenproblem reduction, Sec. 1.1: S = L L^H,
+C = L^{-1} H L^{-H}) with the CPU FP64 oracle.
+
+Tolerance: to first order the forward error of a backward-stable Cholesky and
+of triangular solves is bounded by n u kappa(S) relative to the result
+(u = 2^-53), so every comparison uses max(1e-13, n u kappa(S)) with kappa the
+2-norm condition number of the case's S.  L's strict upper triangle must be
+exactly zero, and C exactly Hermitian with an exactly real diagonal.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import rel_frobenius  # noqa: E402
+from oracle.reduce import reduce_standard  # noqa: E402
+from paper_1611_00606_gb300 import synth  # noqa: E402
+
+U_ROUND = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def hs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_00606_gb300 import hs as _hs
+    return _hs
+
+
+def _dev(X):
+    """numpy (n, n) -> column-major complex128 CUDA tensor."""
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(X, np.complex128).T)).cuda().T
+
+
+def _tol(S):
+    w = np.linalg.eigvalsh(S)  # kappa_2 of a Hermitian positive definite S
+    kappa = w[-1] / w[0] if w[0] > 0 else np.inf
+    return max(1e-13, S.shape[0] * U_ROUND * kappa)
+
+
+def _reduce(hs, H, S, n_max=None):
+    n = H.shape[0]
+    with hs.Plan(1, 1, n_max or max(n, 1)) as p:
+        Hd, Sd = _dev(H), _dev(S)
+        info = p.reduce(Hd, Sd)
+    torch.cuda.synchronize()
+    return Hd.cpu().numpy(), Sd.cpu().numpy(), info
+
+
+def _check(C, L, H, S):
+    Lr, Cr, fail = reduce_standard(H, S)
+    assert fail == 0
+    tol = _tol(S)
+    assert np.all(np.triu(L, 1) == 0)
+    assert rel_frobenius(L, Lr) <= tol, (rel_frobenius(L, Lr), tol)
+    assert rel_frobenius(C, Cr) <= tol, (rel_frobenius(C, Cr), tol)
+    assert np.array_equal(C, C.conj().T)
+    assert np.all(np.diag(C).imag == 0)
+    return rel_frobenius(L, Lr), rel_frobenius(C, Cr)
+
+
+@pytest.mark.parametrize("n,cond", [
+    (1, 1.0),        # one element: L = sqrt(s), C = h / s
+    (37, 1e3),       # inside one 64-tile
+    (64, 1e3),       # exactly one tile
+    (65, 1e3),       # one tile plus a 1-wide tail
+    (130, 1e4),      # three tiles, ragged
+    (257, 1e3),      # five tiles, 1-wide tail; several Cholesky panels
+    (520, 1e6),      # nine panels, ragged, ill-conditioned
+])
+def test_reduce_parity(hs, n, cond):
+    H, S = synth.reduce_inputs(n, seed=n + 7, cond=cond)
+    C, L, info = _reduce(hs, H, S)
+    eL, eC = _check(C, L, H, S)
+    print(f"n={n} cond={cond:g}: L {eL:.2e} C {eC:.2e} ms {info['ms_total']:.3f}")
+    assert info["fail_col"] == 0
+
+
+def test_reduce_reads_lower_triangles_only(hs):
+    n = 150
+    H, S = synth.reduce_inputs(n, seed=3)
+    C1, L1, _ = _reduce(hs, H, S)
+    Hp, Sp = H.copy(), S.copy()
+    iu = np.triu_indices(n, 1)
+    Hp[iu] = np.nan
+    Sp[iu] = 1e300
+    Hp[np.diag_indices(n)] += 5j  # the diagonal enters as its real part
+    C2, L2, _ = _reduce(hs, Hp, Sp)
+    assert np.array_equal(C1, C2) and np.array_equal(L1, L2)
+
+
+@pytest.mark.parametrize("n,col,val", [(100, 71, -1.0), (200, 130, np.nan), (70, 1, 0.0)])
+def test_reduce_not_positive_definite(hs, n, col, val):
+    H, _ = synth.reduce_inputs(n, seed=5)
+    S = np.eye(n, dtype=np.complex128)
+    S[col - 1, col - 1] = val
+    assert reduce_standard(H, S)[2] == col
+    Hd, Sd = _dev(H), _dev(S)
+    with hs.Plan(1, 1, n) as p:
+        with pytest.raises(hs.HSError) as e:
+            p.reduce(Hd, Sd)
+    assert e.value.code == hs.HS_ENOTPD and e.value.fail_col == col
+    assert np.array_equal(Hd.cpu().numpy(), H)  # H untouched
+
+
+def test_reduce_of_assembled_overlap(hs):
+    """The consumer path: H, S from hs_assemble (FP64), then hs_reduce."""
+    w = synth.Workload("r", 4, 36, 200, (1,), seed=19)  # 2K = 288 >= N_G: S definite
+    d = synth.make_inputs(w)
+    A, B = hs.to_device_coef(d["A"]), hs.to_device_coef(d["B"])
+    T = [hs.to_device_T(d[k]) for k in ("T_AA", "T_AB", "T_BB")]
+    U = hs.to_device_U(d["U"])
+    with hs.Plan(w.N_A, w.N_L, w.N_G, "fp64") as p:
+        Hd, Sd, _ = p.assemble(A, B, *T, U)
+        H0, S0 = Hd.cpu().numpy(), Sd.cpu().numpy()
+        p.reduce(Hd, Sd)
+    C, L = Hd.cpu().numpy(), Sd.cpu().numpy()
+    eL, eC = _check(C, L, H0, S0)
+    print(f"assembled N_G=200: L {eL:.2e} C {eC:.2e}")
+
+
+def test_reduce_paper_scale(hs):
+    """auag_like_4000 (N_G = 4000) from the split assembly in the benchmark's launch
+    configuration, then the reduction; the whole result against the oracle."""
+    w = synth.WORKLOADS["auag_like_4000"]
+    d = synth.make_inputs(w)
+    A, B = hs.to_device_coef(d["A"]), hs.to_device_coef(d["B"])
+    T = [hs.to_device_T(d[k]) for k in ("T_AA", "T_AB", "T_BB")]
+    U = hs.to_device_U(d["U"])
+    with hs.Plan(w.N_A, w.N_L, w.N_G, "split_bf16") as p:
+        Hd, Sd, _ = p.assemble(A, B, *T, U)
+        H0, S0 = Hd.cpu().numpy(), Sd.cpu().numpy()
+        info = p.reduce(Hd, Sd)
+    C, L = Hd.cpu().numpy(), Sd.cpu().numpy()
+    eL, eC = _check(C, L, H0, S0)
+    print(f"auag_like_4000: L {eL:.2e} C {eC:.2e} "
+          f"ms {info['ms_total']:.1f}")
+
+
+def test_reduce_deterministic(hs):
+    H, S = synth.reduce_inputs(300, seed=9)
+    C1, L1, _ = _reduce(hs, H, S)
+    C2, L2, _ = _reduce(hs, H, S)
+    assert np.array_equal(C1, C2) and np.array_equal(L1, L2)
+
+
+def test_reduce_misuse(hs):
+    H, S = synth.reduce_inputs(20, seed=2)
+    Hd, Sd = _dev(H), _dev(S)
+    with hs.Plan(1, 1, 10) as p:  # N_G above N_G_max
+        with pytest.raises(hs.HSError) as e:
+            hs.hs_reduce(p.h, Hd, Sd, 20)
+        assert e.value.code == hs.HS_EINVAL
+    with hs.Plan(1, 1, 20) as p:
+        with pytest.raises(hs.HSError) as e:  # H and S the same buffer
+            hs.hs_reduce(p.h, Hd, Hd, 20)
+        assert e.value.code == hs.HS_EINVAL
+        assert hs._lib.hs_reduce(p.h, Hd.data_ptr(), Sd.data_ptr(), 0, None) == hs.HS_OK
+    with hs.Plan(1, 1, 20, "fp64_real") as p:  # real plans: not supported
+        with pytest.raises(hs.HSError) as e:
+            hs.hs_reduce(p.h, Hd, Sd, 20)
+        assert e.value.code == hs.HS_EINVAL
+    assert np.array_equal(Hd.cpu().numpy(), H) and np.array_equal(Sd.cpu().numpy(), S)
