@@ -53,8 +53,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop
 # DRAM bytes (read + write) of one H-contraction launch on auag_like_4000, split s = 5,
 # from ncu (profiles/k_split_gemm_contract_H_auag_like_4000_traffic.md), valid only
 # while the kernel source is the one measured (first 16 hex digits of its sha256).
-MEASURED_TRAFFIC = {"kernel_src_sha256": "95b2ede5693120e7", "workload": "auag_like_4000", "slices": 5,
-                    "bytes": 21610000000 + 159000000}
+MEASURED_TRAFFIC = {"kernel_src_sha256": "c816a02cb3e8b753", "workload": "auag_like_4000", "slices": 5,
+                    "bytes": 20675000000 + 157000000}
 KERNEL_SRC = os.path.join(ROOT, "paper_1611_00606_gb300", "csrc", "k_split.cu")
 
 
@@ -255,8 +255,10 @@ def run_real(args, w):
 
 def run_reduce(args, w):
     """Generalized-eigenproblem reduction (Sec. 1.1) of the workload's H, S; one JSON
-    line (one GPU).  Each step restores H, S from device copies (outside the timed
-    calls) and runs hs_reduce; the device time is the library's CUDA events."""
+    line (one GPU).  Both forms of hs_reduce: split (value; the two-sided products on
+    the BF16 slice path) and FP64 (beside it).  Each step restores H, S from device
+    copies (outside the timed calls) and runs hs_reduce; the device time is the
+    library's CUDA events on its stream."""
     import torch
     from paper_1611_00606_gb300 import hs
     torch.cuda.set_device(0)
@@ -269,29 +271,40 @@ def run_reduce(args, w):
     del d
     plan = hs.hs_plan(w.N_A, w.N_L, n, "split_bf16", args.slices)
     H0, S0, _ = hs.hs_assemble(plan, A, B, *T, U, w.N_A, w.N_L, n)
+    hs.hs_destroy(plan)
     del A, B
     H, S = hs.empty_hs(n, dev), hs.empty_hs(n, dev)
     Fp = _flops.reduce_flops(n)
     F = sum(Fp.values())
+    nblk = (n + 63) // 64
+    forms, results = {}, {}
+    clocks = None
+    for prec, steps in (("split_bf16", args.steps), ("fp64", max(1, args.fp64_steps))):
+        plan = hs.hs_plan(1, 1, n, prec, args.slices if prec == "split_bf16" else 0)
 
-    def one():
-        H.copy_(H0)
-        S.copy_(S0)
-        return hs.hs_reduce(plan, H, S, n)
-    for _ in range(max(1, args.warmup)):
-        one()
-    torch.cuda.synchronize()
-    clk = ClockSampler(torch.cuda.current_device())
-    clk.start()
-    infos = [one() for _ in range(args.steps)]
-    clocks = clk.stop()
-    ms = sum(i["ms_total"] for i in infos) / len(infos)
-    phase = {k: sum(i[k] for i in infos) / len(infos)
-             for k in ("ms_cholesky", "ms_inverse", "ms_p", "ms_g")}
-    # per step: Cholesky 3 nblk - 1 (diagonal blocks, panels, trailing updates, zeroing),
-    # inverse 2 nblk (identity, diagonal blocks, updates), P, G, G + G^H
-    launches = 5 * ((n + 63) // 64) + 2
-    cpu, err = None, None
+        def one():
+            H.copy_(H0)
+            S.copy_(S0)
+            return hs.hs_reduce(plan, H, S, n)
+        for _ in range(max(1, args.warmup)):
+            one()
+        torch.cuda.synchronize()
+        clk = ClockSampler(torch.cuda.current_device())
+        clk.start()
+        infos = [one() for _ in range(steps)]
+        c = clk.stop()
+        clocks = clocks or c
+        hs.hs_destroy(plan)
+        ms = sum(i["ms_total"] for i in infos) / len(infos)
+        phase = {k: round(sum(i[k] for i in infos) / len(infos), 3)
+                 for k in ("ms_cholesky", "ms_inverse", "ms_p", "ms_g")}
+        # launches per step: Cholesky 3 nblk - 1, inverse 2 nblk; then FP64: P, G, G + G^H;
+        # split: transpose, mirror, 2 slicer launches, contraction, slicer, contraction, mirror
+        launches = 5 * nblk - 1 + (3 if prec == "fp64" else 8)
+        forms[prec] = {"ms_per_step": ms, "tflops": F / ms / 1e9, "steps": steps,
+                       "phase_ms": phase, "gpu_launches": launches * steps, "clocks": c}
+        results[prec] = (H.cpu().numpy(), S.cpu().numpy())
+    cpu = None
     if not args.no_cpu_baseline:
         # CPU baseline leg: the FP64 oracle's reduction of the same H, S (whole problem)
         from oracle import rel_frobenius
@@ -303,26 +316,30 @@ def run_reduce(args, w):
         cpu = {"value": F / t / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"the whole reduction of {w.name}'s H, S (N_G = {n}) by the oracle "
                          f"(numpy Cholesky + two triangular solves), {t:.1f} s; same flop count"}
-        err = {"L": rel_frobenius(S.cpu().numpy(), Lr), "C": rel_frobenius(H.cpu().numpy(), Cr)}
-    hs.hs_destroy(plan)
-    gemm_g = Fp["g"] / (phase["ms_g"] / 1e3) / 1e12
+        for prec, (C, L) in results.items():
+            forms[prec]["rel_frobenius_vs_oracle"] = {"L": rel_frobenius(L, Lr),
+                                                      "C": rel_frobenius(C, Cr)}
+    sp, f64 = forms["split_bf16"], forms["fp64"]
+    fp64_tf = Fp["cholesky"] / (sp["phase_ms"]["ms_cholesky"] / 1e3) / 1e12
+    gemm_g = Fp["g"] / (f64["phase_ms"]["ms_g"] / 1e3) / 1e12
     line = {"metric": "generalized-eigenproblem reduction TFLOP/s (S = L L^H, C = L^-1 H L^-H; "
-                      "20/3 N_G^3 executed flops) per k-point",
-            "value": F / ms / 1e9, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "20/3 N_G^3 flops of the FP64 algorithm) per k-point",
+            "value": sp["tflops"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sp["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": f"f64 Cholesky and inverse; bf16 slices x{args.slices} for the two-sided "
+                     "products", "data": "synthetic",
             "config": {"workload": f"{_wl_desc(w)}: H, S from the split assembly",
                        "l2": "H, S 0.26 GB each (> L2), restored before each step"},
-            "lapack_equivalent_tflops": _flops.reduce_flops_lapack(n) / ms / 1e9,
-            "phase_ms": {k: round(v, 3) for k, v in phase.items()},
-            "roofline": {"bound": "alu", "kernel": "k_zgemm (G = P W^H)", "achieved": gemm_g,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "forms": forms,
+            "speedup_vs_fp64_form": f64["ms_per_step"] / sp["ms_per_step"],
+            "roofline": {"bound": "alu", "kernel": "k_zgemm (FP64 form: G = P W^H)",
+                         "achieved": gemm_g, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": gemm_g / FP64_PEAK_TFLOPS, "traffic": None,
                          "work": "8/3 N_G^3 flops of G = P W^H (FP64 DFMA)",
                          "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz",
-                         "step_frac": (F / ms / 1e9) / FP64_PEAK_TFLOPS},
-            "cpu_baseline": cpu, "rel_frobenius_vs_oracle": err, "gpu_launches": launches * args.steps,
-            "clocks": clocks}
+                         "split_cholesky_frac": fp64_tf / FP64_PEAK_TFLOPS},
+            "cpu_baseline": cpu, "gpu_launches": sp["gpu_launches"], "clocks": clocks}
     print(json.dumps(line))
     return 0
 

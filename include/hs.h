@@ -210,11 +210,16 @@ int hs_assemble_static(const hs_z* A, const hs_z* B, const hs_z* T_AA, const hs_
  *                 c = L^{-H} y.
  * H and S are DEVICE pointers, N_G x N_G column-major with leading dimension N_G
  * (the layout hs_assemble writes).  Only the lower triangles are read (H's
- * diagonal as its real part).  FP64 in every plan precision (the kernels are
- * bound by the FP64 pipe: 20/3 N_G^3 real flops).  Complex plans only (real plans:
- * HS_EINVAL).  0 <= N_G <= N_G_max.  The plan allocates 32 N_G^2 bytes of device
- * workspace on first use (grown on demand, freed by hs_destroy); HS_ENOMEM if that
- * fails.  Runs on the plan's stream and returns when done.
+ * diagonal as its real part).  The Cholesky and the triangular inverse are FP64 in
+ * every plan precision.  The two-sided products: FP64 (DFMA) on HS_FP64 plans;
+ * on HS_SPLIT_BF16 plans two BF16 slice contractions on the tensor cores with the
+ * plan's slice count (H L^{-H}, then C = Z^H B + B^H Z with B = L^{-H} and
+ * Z = H B / 2), relative error about 1e-10 kappa(S) instead of FP64's.  Complex plans
+ * only (real plans: HS_EINVAL).  0 <= N_G <= N_G_max.  The plan allocates 32 N_G^2
+ * bytes of device workspace on first use (split plans also about (24 s + 32) N_G^2
+ * bytes of slices and products), grown on demand and
+ * freed by hs_destroy; HS_ENOMEM if that fails.  Runs on the plan's stream and
+ * returns when done.
  * HS_ENOTPD: a Cholesky pivot of S is zero, negative or NaN; info->fail_col is that
  * column (1-based), H is unchanged and S holds a partial factor.
  * info may be NULL. */

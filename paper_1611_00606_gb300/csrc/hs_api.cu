@@ -125,6 +125,7 @@ void hs_plan_s::release() {
   free_ptr((void*&)red_P);
   free_ptr((void*&)red_fail);
   red_cap = 0;
+  split_reduce_release();
   for (auto& e : red_ev)
     if (e) { cudaEventDestroy(e); e = nullptr; }
   for (auto& e : copy_ev)
@@ -606,23 +607,48 @@ extern "C" int hs_reduce(hs_plan_t p, hs_z* H, hs_z* S, int N_G, hs_reduce_info*
   }
   for (auto& e : p->red_ev)
     if (!e) HS_CUDA_TRY(cudaEventCreate(&e));
+  const bool split = p->precision == HS_SPLIT_BF16;
+  if (split) {
+    const int rc = p->split_reduce_alloc(N_G);
+    if (rc) return rc;
+  }
   cudaStream_t st = p->stream;
   double2* dH = (double2*)H;
   double2* dS = (double2*)S;
+  int fail = 0;
   HS_CUDA_TRY(cudaMemsetAsync(p->red_fail, 0, sizeof(int), st));
   HS_CUDA_TRY(cudaEventRecord(p->red_ev[0], st));
   HS_CUDA_TRY(hs_launch_cholesky(dS, N_G, p->red_fail, st));
   HS_CUDA_TRY(cudaEventRecord(p->red_ev[1], st));
+  if (split) {  // the slice path does not read the failure word: stop here if S failed
+    HS_CUDA_TRY(cudaMemcpyAsync(&fail, p->red_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (fail) {
+      if (info) info->fail_col = fail;
+      return HS_ENOTPD;
+    }
+  }
   HS_CUDA_TRY(hs_launch_tri_inverse(dS, p->red_W, N_G, p->red_fail, st));
   HS_CUDA_TRY(cudaEventRecord(p->red_ev[2], st));
-  HS_CUDA_TRY(hs_launch_reduce_p(p->red_W, dH, p->red_P, N_G, p->red_fail, st));
-  HS_CUDA_TRY(cudaEventRecord(p->red_ev[3], st));
-  HS_CUDA_TRY(hs_launch_reduce_g(p->red_P, p->red_W, dH, N_G, p->red_fail, st));
-  HS_CUDA_TRY(hs_launch_hermsum(dH, N_G, p->red_fail, st));
+  if (split) {
+    // B = W^H; H completed from its lower triangle; then H <- B^H H B on the tensor cores
+    HS_CUDA_TRY(hs_launch_ctrans(p->red_W, N_G, p->red_P, st));
+    HS_CUDA_TRY(hs_launch_mirror(dH, N_G, N_G, st));
+    const int rc = p->split_reduce_transform(p->red_P, dH, N_G, st, p->red_ev[3]);
+    if (rc) return rc;
+  } else {
+    HS_CUDA_TRY(hs_launch_reduce_p(p->red_W, dH, p->red_P, N_G, p->red_fail, st));
+    HS_CUDA_TRY(cudaEventRecord(p->red_ev[3], st));
+    HS_CUDA_TRY(hs_launch_reduce_g(p->red_P, p->red_W, dH, N_G, p->red_fail, st));
+    HS_CUDA_TRY(hs_launch_hermsum(dH, N_G, p->red_fail, st));
+  }
   HS_CUDA_TRY(cudaEventRecord(p->red_ev[4], st));
-  int fail = 0;
   HS_CUDA_TRY(cudaMemcpyAsync(&fail, p->red_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
   HS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (split) {
+    const int rc = p->check_device_error();
+    if (rc) return rc;
+  }
   if (info) {
     auto el = [&](int a, int b) {
       float ms = 0.f;

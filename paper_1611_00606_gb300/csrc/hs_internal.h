@@ -71,6 +71,8 @@ cudaError_t hs_launch_reduce_g(const double2* P, const double2* W, double2* H, i
                                const int* fail, cudaStream_t st);
 // H <- H + H^H (diagonal exactly real).
 cudaError_t hs_launch_hermsum(double2* H, int n, const int* fail, cudaStream_t st);
+// B <- A^H (n x n).
+cudaError_t hs_launch_ctrans(const double2* A, int n, double2* B, cudaStream_t st);
 
 // ---- real-symmetric variant helpers (k_real.cu) --------------------------------
 // y[i] = (x[i], 0) for i < n.

@@ -329,6 +329,22 @@ __global__ void k_hermsum(double2* __restrict__ C, int n, int ld, const int* __r
   }
 }
 
+// B = A^H (n x n, leading dimensions n), 32 x 32 blocks through shared memory.
+__global__ void k_ctrans(const double2* __restrict__ A, int n, double2* __restrict__ B) {
+  __shared__ double2 t[32][33];
+  const int bx = blockIdx.x, by = blockIdx.y;    // source block: rows by, columns bx
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    const int i = by * 32 + tx, j = bx * 32 + k;  // t[k][tx] = A(i, j)
+    t[k][tx] = (i < n && j < n) ? A[i + (size_t)j * n] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int i = bx * 32 + tx, j = by * 32 + k;  // B(i, j) = conj(A(j, i)) = conj(t[tx][k])
+    if (i < n && j < n) B[i + (size_t)j * n] = zconj(t[tx][k]);
+  }
+}
+
 cudaError_t zgemm(const ZgemmArgs& g, cudaStream_t st) {
   if (g.m <= 0 || g.n <= 0) return cudaSuccess;
   const dim3 grid((g.n + RT - 1) / RT, (g.m + RT - 1) / RT);
@@ -451,6 +467,12 @@ cudaError_t hs_launch_reduce_g(const double2* P, const double2* W, double2* H, i
   g.triA = 1;
   g.triB = 1;
   return zgemm(g, st);
+}
+
+cudaError_t hs_launch_ctrans(const double2* A, int n, double2* B, cudaStream_t st) {
+  const int nb = (n + 31) / 32;
+  k_ctrans<<<dim3(nb, nb), dim3(32, 8), 0, st>>>(A, n, B);
+  return cudaGetLastError();
 }
 
 cudaError_t hs_launch_hermsum(double2* H, int n, const int* fail, cudaStream_t st) {

@@ -39,6 +39,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -1883,4 +1884,153 @@ int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const
   rc = split_atoms(&job, 1, st, nullptr);
   if (rc) return rc;
   return split_outputs(A, ldAB, N_G, H, S, w, st, timed, s_done, presliced);
+}
+
+// ---------------------------------------------------------------------------
+// hs_reduce on split plans: the two-sided transform C = L^{-1} H L^{-H} (Sec. 1.1) as
+// two BF16 slice contractions.  With B = L^{-H} (upper triangular) and Z = H B / 2,
+// C = Z^H B + B^H Z.  The full product H B comes from the lower triangle of M^H M for
+// the stacked operand M = [B | 0 | H] (n complex rows; B at columns [0, n), zeros up
+// to n_pad = rows_pad_of(n), H at [n_pad, n_pad + n)): below the split, its row blocks
+// hold H^H B = H B, K-major as the next contraction reads it.  Only those row blocks
+// are launched (bi0 = n_pad / BM), written through a base shifted back by n_pad rows.
+// The second contraction reads B's slices as M's first n rows.
+
+void hs_plan_s::split_reduce_release() {
+  for (SliceBuf* b : {&red_M, &red_Zs}) {
+    if (b->plain) cudaFree(b->plain);
+    if (b->rot) cudaFree(b->rot);
+    if (b->expo) cudaFree(b->expo);
+    *b = SliceBuf{};
+  }
+  if (red_Z) cudaFree(red_Z);
+  if (red_half) cudaFree(red_half);
+  red_Z = nullptr;
+  red_half = nullptr;
+  red_split_cap = 0;
+}
+
+int hs_plan_s::split_reduce_alloc(int n) {
+  if (red_split_cap >= n) return HS_OK;
+  split_reduce_release();
+  if (!get_encode()) return HS_ECUDA;
+  const int n_pad = rows_pad_of(n), NM = n_pad + n;
+  const int rpM = rows_pad_of(NM), rp = rows_pad_of(n);
+  const size_t kpad = (size_t)kpad_of(n, 1);
+  const size_t oneM = (size_t)slices * rpM * kpad * 2, oneZ = (size_t)slices * rp * kpad * 2;
+  const bool ok =
+      cudaMalloc((void**)&red_M.plain, oneM) == cudaSuccess &&
+      cudaMalloc((void**)&red_M.rot, oneM) == cudaSuccess &&
+      cudaMalloc((void**)&red_M.expo, sizeof(int) * rpM) == cudaSuccess &&
+      cudaMalloc((void**)&red_Zs.plain, oneZ) == cudaSuccess &&
+      cudaMalloc((void**)&red_Zs.rot, oneZ) == cudaSuccess &&
+      cudaMalloc((void**)&red_Zs.expo, sizeof(int) * rp) == cudaSuccess &&
+      cudaMalloc((void**)&red_Z, sizeof(double2) * (size_t)n * NM) == cudaSuccess &&
+      cudaMalloc((void**)&red_half, sizeof(double) * (size_t)n) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    split_reduce_release();
+    return HS_ENOMEM;
+  }
+  std::vector<double> half((size_t)n, 0.5);
+  if (cudaMemcpy(red_half, half.data(), sizeof(double) * n, cudaMemcpyHostToDevice) !=
+      cudaSuccess) {
+    split_reduce_release();
+    return HS_ECUDA;
+  }
+  red_split_cap = n;
+  return HS_OK;
+}
+
+static int contract_tiles(const SplitParams& P) {
+  int tiles = 0;
+  for (int b = P.bi0; b < P.nbi; ++b) tiles += 2 * std::min(b + 1, (P.nbj + 1) / 2);
+  return tiles;
+}
+
+int hs_plan_s::split_reduce_transform(const double2* B, double2* H, int n, cudaStream_t st,
+                                      cudaEvent_t mid) {
+  if (precision != HS_SPLIT_BF16 || real || n < 1) return HS_EINVAL;
+  int rc = split_reduce_alloc(n);
+  if (rc) return rc;
+  const int s = slices;
+  const int n_pad = rows_pad_of(n), NM = n_pad + n;
+  const int rpM = rows_pad_of(NM), rp = rows_pad_of(n);
+  const int NKB = kpad_of(n, 1) / KB;
+  int n_stage;
+  size_t smem;
+  rc = split_geometry(n_stage, smem);
+  if (rc) return rc;
+  // 1. slices of M: B (zeros past column n up to n_pad), then H from column n_pad on (the
+  //    source pointer is shifted back so that column g reads H's column g - n_pad)
+  {
+    SliceParams sp{};
+    sp.job[0] = SliceJob{B, nullptr, red_M.plain, red_M.rot, red_M.expo, n, n};
+    rc = slice_launch(sp, 1, s, n, rpM, 1, false, st, 0, n_pad);
+    if (rc) return rc;
+    SliceParams sq{};
+    const double2* Hs =
+        (const double2*)((uintptr_t)H - (uintptr_t)n_pad * (uintptr_t)n * sizeof(double2));
+    sq.job[0] = SliceJob{Hs, nullptr, red_M.plain, red_M.rot, red_M.expo, n, n};
+    rc = slice_launch(sq, 1, s, NM, rpM, 1, false, st, n_pad, -1);
+    if (rc) return rc;
+  }
+  SplitParams* PP = new (std::nothrow) SplitParams;
+  if (!PP) return HS_ENOMEM;
+  std::unique_ptr<SplitParams> own(PP);
+  SplitParams& P = *PP;
+  // 2. H B: row blocks of M's H part against every column block up to the diagonal
+  std::memset(&P, 0, sizeof(P));
+  if (!encode_tiles(&P.maps[0], red_M.plain, NKB, rpM / 64, s) ||
+      !encode_tiles(&P.maps[1], red_M.rot, NKB, rpM / 64, s))
+    return HS_ECUDA;
+  P.seg[0] = SplitSeg{0, 0, 1, NKB, red_M.expo, red_M.expo};
+  P.nseg = 1;
+  P.s = s;
+  P.N_G = NM;
+  P.ldC = n;
+  P.nbj = (NM + BNC - 1) / BNC;
+  P.rows_pad = rpM;
+  P.err = err_d;
+  P.bi0 = n_pad / BM;
+  P.nbi = (NM + BM - 1) / BM;
+  P.band = contract_band();
+  P.ntiles = contract_tiles(P);
+  P.C = (double2*)((uintptr_t)red_Z - (uintptr_t)n_pad * sizeof(double2));  // row n_pad -> 0
+  P.n_stage = n_stage;
+  rc = launch_gemm(MODE_CONTRACT, s, P.ntiles, smem, st, P);
+  if (rc) return rc;
+  if (mid && cudaEventRecord(mid, st) != cudaSuccess) return HS_ECUDA;
+  // 3. slices of Z = (H B) / 2: the first n columns of red_Z, halved by the row weight
+  {
+    SliceParams sz{};
+    sz.job[0] = SliceJob{red_Z, red_half, red_Zs.plain, red_Zs.rot, red_Zs.expo, n, n};
+    rc = slice_launch(sz, 1, s, n, rp, 1, false, st);
+    if (rc) return rc;
+  }
+  // 4. C = Z^H B + B^H Z, lower tiles, into H; then the mirror
+  std::memset(&P, 0, sizeof(P));
+  if (!encode_tiles(&P.maps[0], red_Zs.plain, NKB, rp / 64, s) ||
+      !encode_tiles(&P.maps[1], red_Zs.rot, NKB, rp / 64, s) ||
+      !encode_tiles(&P.maps[2], red_M.plain, NKB, rpM / 64, s) ||
+      !encode_tiles(&P.maps[3], red_M.rot, NKB, rpM / 64, s))
+    return HS_ECUDA;
+  P.seg[0] = SplitSeg{0, 2, 3, NKB, red_Zs.expo, red_M.expo};  // Z^H B
+  P.seg[1] = SplitSeg{2, 0, 1, NKB, red_M.expo, red_Zs.expo};  // B^H Z
+  P.nseg = 2;
+  P.s = s;
+  P.N_G = n;
+  P.ldC = n;
+  P.nbj = (n + BNC - 1) / BNC;
+  P.rows_pad = rp;
+  P.err = err_d;
+  P.bi0 = 0;
+  P.nbi = (n + BM - 1) / BM;
+  P.band = contract_band();
+  P.ntiles = contract_tiles(P);
+  P.C = H;
+  P.n_stage = n_stage;
+  rc = launch_gemm(MODE_CONTRACT, s, P.ntiles, smem, st, P);
+  if (rc) return rc;
+  return hs_launch_mirror(H, n, n, st) == cudaSuccess ? HS_OK : HS_ECUDA;
 }

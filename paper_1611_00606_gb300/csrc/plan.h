@@ -102,6 +102,12 @@ struct hs_plan_s {
   int red_cap = 0;
   int* red_fail = nullptr;
   cudaEvent_t red_ev[5] = {};
+  // hs_reduce, split plans: slices of M = [L^{-H} | 0 | H] and of Z = H L^{-H} / 2,
+  // 2 Z in FP64 (n x (n_pad + n)), the row weight 1/2; sized for red_split_cap
+  SliceBuf red_M, red_Zs;
+  double2* red_Z = nullptr;
+  double* red_half = nullptr;
+  int red_split_cap = 0;
 
   ServeState* serve = nullptr;
 
@@ -144,6 +150,12 @@ struct hs_plan_s {
   // S contraction tiles of row blocks [bi0, bi1) only (no mirror)
   int split_contract_S_rows(int N_G, double2* S, Workspace& w, cudaStream_t st, int bi0,
                             int bi1);
+  // hs_reduce's two-sided transform on the slice path: H <- B^H H B with B = L^{-H}
+  // (n x n column-major, upper triangular); records `mid` between its two contractions
+  int split_reduce_transform(const double2* B, double2* H, int n, cudaStream_t st,
+                             cudaEvent_t mid);
+  int split_reduce_alloc(int n);
+  void split_reduce_release();
   int check_device_error();
   void fill_info(hs_info* info, bool factored);
   bool serve_busy();

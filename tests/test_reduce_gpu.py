@@ -1,11 +1,20 @@
 """Parity of hs_reduce (generalized-eigenproblem reduction, Sec. 1.1: S = L L^H,
 C = L^{-1} H L^{-H}) with the CPU FP64 oracle.
 
-Tolerance: to first order the forward error of a backward-stable Cholesky and
-of triangular solves is bounded by n u kappa(S) relative to the result
-(u = 2^-53), so every comparison uses max(1e-13, n u kappa(S)) with kappa the
-2-norm condition number of the case's S.  L's strict upper triangle must be
-exactly zero, and C exactly Hermitian with an exactly real diagonal.
+Tolerance, FP64 form: to first order the forward error of a backward-stable
+Cholesky and of triangular solves is bounded by n u kappa(S) relative to the
+result (u = 2^-53), so every comparison uses max(1e-13, n u kappa(S)) with kappa
+the 2-norm condition number of the case's S.
+
+Split form (plans of precision split_bf16): the Cholesky and the inverse are the
+same FP64 kernels (L is bitwise equal to the FP64 form's), the two products
+H L^{-H} and Z^H B + B^H Z run on the BF16 slice path, whose results carry a
+relative error of at most the split assembly's 1e-10 of their operands' scale;
+||B||^2 = 1/lambda_min(S) and ||C|| >= ||H|| / lambda_max(S) turn that into
+1e-10 kappa(S) relative to C.
+
+Both forms: L's strict upper triangle is exactly zero, and C exactly Hermitian
+with an exactly real diagonal.
 """
 import numpy as np
 import pytest
@@ -34,27 +43,35 @@ def _dev(X):
     return torch.from_numpy(np.ascontiguousarray(np.asarray(X, np.complex128).T)).cuda().T
 
 
-def _tol(S):
+TOL_SPLIT = 1e-10
+
+
+def _kappa(S):
     w = np.linalg.eigvalsh(S)  # kappa_2 of a Hermitian positive definite S
-    kappa = w[-1] / w[0] if w[0] > 0 else np.inf
-    return max(1e-13, S.shape[0] * U_ROUND * kappa)
+    return w[-1] / w[0] if w[0] > 0 else np.inf
 
 
-def _reduce(hs, H, S, n_max=None):
+def _tol(S, precision="fp64"):
+    if precision == "split_bf16":
+        return TOL_SPLIT * max(1.0, _kappa(S))
+    return max(1e-13, S.shape[0] * U_ROUND * _kappa(S))
+
+
+def _reduce(hs, H, S, precision="fp64"):
     n = H.shape[0]
-    with hs.Plan(1, 1, n_max or max(n, 1)) as p:
+    with hs.Plan(1, 1, max(n, 1), precision) as p:
         Hd, Sd = _dev(H), _dev(S)
         info = p.reduce(Hd, Sd)
     torch.cuda.synchronize()
     return Hd.cpu().numpy(), Sd.cpu().numpy(), info
 
 
-def _check(C, L, H, S):
+def _check(C, L, H, S, precision="fp64"):
     Lr, Cr, fail = reduce_standard(H, S)
     assert fail == 0
-    tol = _tol(S)
+    tol = _tol(S, precision)
     assert np.all(np.triu(L, 1) == 0)
-    assert rel_frobenius(L, Lr) <= tol, (rel_frobenius(L, Lr), tol)
+    assert rel_frobenius(L, Lr) <= _tol(S), (rel_frobenius(L, Lr), _tol(S))
     assert rel_frobenius(C, Cr) <= tol, (rel_frobenius(C, Cr), tol)
     assert np.array_equal(C, C.conj().T)
     assert np.all(np.diag(C).imag == 0)
@@ -78,27 +95,46 @@ def test_reduce_parity(hs, n, cond):
     assert info["fail_col"] == 0
 
 
-def test_reduce_reads_lower_triangles_only(hs):
+@pytest.mark.parametrize("n,cond", [
+    (1, 1.0),
+    (65, 1e3),
+    (130, 1e4),
+    (257, 1e3),      # several row blocks of the stacked operand, ragged
+    (520, 1e6),
+])
+def test_reduce_split_parity(hs, n, cond):
+    H, S = synth.reduce_inputs(n, seed=n + 7, cond=cond)
+    C, L, info = _reduce(hs, H, S, "split_bf16")
+    C64, L64, _ = _reduce(hs, H, S, "fp64")
+    assert np.array_equal(L, L64)  # the factor is FP64 in both forms
+    eL, eC = _check(C, L, H, S, "split_bf16")
+    print(f"split n={n} cond={cond:g}: C {eC:.2e} (fp64 form {rel_frobenius(C64, C):.2e} apart) "
+          f"ms {info['ms_total']:.3f}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
+def test_reduce_reads_lower_triangles_only(hs, precision):
     n = 150
     H, S = synth.reduce_inputs(n, seed=3)
-    C1, L1, _ = _reduce(hs, H, S)
+    C1, L1, _ = _reduce(hs, H, S, precision)
     Hp, Sp = H.copy(), S.copy()
     iu = np.triu_indices(n, 1)
     Hp[iu] = np.nan
     Sp[iu] = 1e300
     Hp[np.diag_indices(n)] += 5j  # the diagonal enters as its real part
-    C2, L2, _ = _reduce(hs, Hp, Sp)
+    C2, L2, _ = _reduce(hs, Hp, Sp, precision)
     assert np.array_equal(C1, C2) and np.array_equal(L1, L2)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
 @pytest.mark.parametrize("n,col,val", [(100, 71, -1.0), (200, 130, np.nan), (70, 1, 0.0)])
-def test_reduce_not_positive_definite(hs, n, col, val):
+def test_reduce_not_positive_definite(hs, n, col, val, precision):
     H, _ = synth.reduce_inputs(n, seed=5)
     S = np.eye(n, dtype=np.complex128)
     S[col - 1, col - 1] = val
     assert reduce_standard(H, S)[2] == col
     Hd, Sd = _dev(H), _dev(S)
-    with hs.Plan(1, 1, n) as p:
+    with hs.Plan(1, 1, n, precision) as p:
         with pytest.raises(hs.HSError) as e:
             p.reduce(Hd, Sd)
     assert e.value.code == hs.HS_ENOTPD and e.value.fail_col == col
@@ -123,26 +159,34 @@ def test_reduce_of_assembled_overlap(hs):
 
 def test_reduce_paper_scale(hs):
     """auag_like_4000 (N_G = 4000) from the split assembly in the benchmark's launch
-    configuration, then the reduction; the whole result against the oracle."""
+    configuration, then the reduction in both forms; the whole results against the
+    oracle."""
     w = synth.WORKLOADS["auag_like_4000"]
     d = synth.make_inputs(w)
     A, B = hs.to_device_coef(d["A"]), hs.to_device_coef(d["B"])
     T = [hs.to_device_T(d[k]) for k in ("T_AA", "T_AB", "T_BB")]
     U = hs.to_device_U(d["U"])
     with hs.Plan(w.N_A, w.N_L, w.N_G, "split_bf16") as p:
-        Hd, Sd, _ = p.assemble(A, B, *T, U)
-        H0, S0 = Hd.cpu().numpy(), Sd.cpu().numpy()
+        H0d, S0d, _ = p.assemble(A, B, *T, U)
+        H0, S0 = H0d.cpu().numpy(), S0d.cpu().numpy()
+        Hd, Sd = H0d.clone(), S0d.clone()
         info = p.reduce(Hd, Sd)
     C, L = Hd.cpu().numpy(), Sd.cpu().numpy()
-    eL, eC = _check(C, L, H0, S0)
-    print(f"auag_like_4000: L {eL:.2e} C {eC:.2e} "
-          f"ms {info['ms_total']:.1f}")
+    eL, eC = _check(C, L, H0, S0, "split_bf16")
+    with hs.Plan(1, 1, w.N_G, "fp64") as p:
+        info64 = p.reduce(H0d, S0d)
+    C64, L64 = H0d.cpu().numpy(), S0d.cpu().numpy()
+    assert np.array_equal(L, L64)
+    eL64, eC64 = _check(C64, L64, H0, S0)
+    print(f"auag_like_4000: split C {eC:.2e} ms {info['ms_total']:.1f}; "
+          f"fp64 L {eL64:.2e} C {eC64:.2e} ms {info64['ms_total']:.1f}")
 
 
-def test_reduce_deterministic(hs):
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
+def test_reduce_deterministic(hs, precision):
     H, S = synth.reduce_inputs(300, seed=9)
-    C1, L1, _ = _reduce(hs, H, S)
-    C2, L2, _ = _reduce(hs, H, S)
+    C1, L1, _ = _reduce(hs, H, S, precision)
+    C2, L2, _ = _reduce(hs, H, S, precision)
     assert np.array_equal(C1, C2) and np.array_equal(L1, L2)
 
 
