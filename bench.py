@@ -53,8 +53,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop
 # DRAM bytes (read + write) of one H-contraction launch on auag_like_4000, split s = 5,
 # from ncu (profiles/k_split_gemm_contract_H_auag_like_4000_traffic.md), valid only
 # while the kernel source is the one measured (first 16 hex digits of its sha256).
-MEASURED_TRAFFIC = {"kernel_src_sha256": "c816a02cb3e8b753", "workload": "auag_like_4000", "slices": 5,
-                    "bytes": 20675000000 + 157000000}
+MEASURED_TRAFFIC = {"kernel_src_sha256": "82227e2d0cbf4fd1", "workload": "auag_like_4000", "slices": 5,
+                    "bytes": 20819000000 + 158000000}
 KERNEL_SRC = os.path.join(ROOT, "paper_1611_00606_gb300", "csrc", "k_split.cu")
 
 
@@ -253,6 +253,27 @@ def run_real(args, w):
     return 0
 
 
+def _reduce_launches(n: int, split: bool) -> int:
+    """Kernel launches of one hs_reduce call (the library's launch sequence)."""
+    pw_max = 256 if split else n
+    cnt = 0
+    for j0 in range(0, n, pw_max):  # Cholesky panels: diagonal blocks, panels, updates
+        pw = min(pw_max, n - j0)
+        for jj in range(j0, j0 + pw, 64):
+            r0 = jj + min(64, j0 + pw - jj)
+            cnt += 1 + (n > r0) + (n > r0 and j0 + pw > r0)
+        cnt += 4 if n - j0 - pw > 0 else 0  # transpose, slicer, contraction, subtraction
+    cnt += 2  # zeroing of the upper triangle, identity
+    for i0 in range(0, n, pw_max):  # inverse block rows: diagonal blocks, updates
+        pw = min(pw_max, n - i0)
+        for ii in range(i0, i0 + pw, 64):
+            cnt += 1 + (i0 + pw > ii + min(64, i0 + pw - ii))
+        cnt += 5 if n - i0 - pw > 0 else 0  # transpose, 2 slicer launches, contraction, subtraction
+    # two-sided products: FP64 P, G, G + G^H; split: transpose, mirror, 2 slicer
+    # launches, contraction, slicer, contraction, mirror
+    return cnt + (8 if split else 3)
+
+
 def run_reduce(args, w):
     """Generalized-eigenproblem reduction (Sec. 1.1) of the workload's H, S; one JSON
     line (one GPU).  Both forms of hs_reduce: split (value; the two-sided products on
@@ -298,9 +319,7 @@ def run_reduce(args, w):
         ms = sum(i["ms_total"] for i in infos) / len(infos)
         phase = {k: round(sum(i[k] for i in infos) / len(infos), 3)
                  for k in ("ms_cholesky", "ms_inverse", "ms_p", "ms_g")}
-        # launches per step: Cholesky 3 nblk - 1, inverse 2 nblk; then FP64: P, G, G + G^H;
-        # split: transpose, mirror, 2 slicer launches, contraction, slicer, contraction, mirror
-        launches = 5 * nblk - 1 + (3 if prec == "fp64" else 8)
+        launches = _reduce_launches(n, prec == "split_bf16")
         forms[prec] = {"ms_per_step": ms, "tflops": F / ms / 1e9, "steps": steps,
                        "phase_ms": phase, "gpu_launches": launches * steps, "clocks": c}
         results[prec] = (H.cpu().numpy(), S.cpu().numpy())

@@ -210,11 +210,13 @@ int hs_assemble_static(const hs_z* A, const hs_z* B, const hs_z* T_AA, const hs_
  *                 c = L^{-H} y.
  * H and S are DEVICE pointers, N_G x N_G column-major with leading dimension N_G
  * (the layout hs_assemble writes).  Only the lower triangles are read (H's
- * diagonal as its real part).  The Cholesky and the triangular inverse are FP64 in
- * every plan precision.  The two-sided products: FP64 (DFMA) on HS_FP64 plans;
- * on HS_SPLIT_BF16 plans two BF16 slice contractions on the tensor cores with the
- * plan's slice count (H L^{-H}, then C = Z^H B + B^H Z with B = L^{-H} and
- * Z = H B / 2), relative error about 1e-10 kappa(S) instead of FP64's.  Complex plans
+ * diagonal as its real part).  HS_FP64 plans: FP64 (DFMA) throughout, blocked
+ * Cholesky, triangular inverse W = L^{-1} and the products C = G + G^H with
+ * G = W tril(H) W^H.  HS_SPLIT_BF16 plans: the Cholesky and the inverse factor
+ * 256-wide panels in FP64 and run their trailing updates, and the two-sided products
+ * (H L^{-H}, then C = Z^H B + B^H Z with B = L^{-H} and Z = H B / 2), as BF16 slice
+ * contractions on the tensor cores with the plan's slice count; relative error about
+ * 1e-10 kappa(S) instead of FP64's.  Complex plans
  * only (real plans: HS_EINVAL).  0 <= N_G <= N_G_max.  The plan allocates 32 N_G^2
  * bytes of device workspace on first use (split plans also about (24 s + 32) N_G^2
  * bytes of slices and products), grown on demand and

@@ -618,7 +618,12 @@ extern "C" int hs_reduce(hs_plan_t p, hs_z* H, hs_z* S, int N_G, hs_reduce_info*
   int fail = 0;
   HS_CUDA_TRY(cudaMemsetAsync(p->red_fail, 0, sizeof(int), st));
   HS_CUDA_TRY(cudaEventRecord(p->red_ev[0], st));
-  HS_CUDA_TRY(hs_launch_cholesky(dS, N_G, p->red_fail, st));
+  if (split) {
+    const int rc = p->split_cholesky(dS, N_G, p->red_fail, st);
+    if (rc) return rc;
+  } else {
+    HS_CUDA_TRY(hs_launch_cholesky(dS, N_G, p->red_fail, st));
+  }
   HS_CUDA_TRY(cudaEventRecord(p->red_ev[1], st));
   if (split) {  // the slice path does not read the failure word: stop here if S failed
     HS_CUDA_TRY(cudaMemcpyAsync(&fail, p->red_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -628,11 +633,16 @@ extern "C" int hs_reduce(hs_plan_t p, hs_z* H, hs_z* S, int N_G, hs_reduce_info*
       return HS_ENOTPD;
     }
   }
-  HS_CUDA_TRY(hs_launch_tri_inverse(dS, p->red_W, N_G, p->red_fail, st));
+  if (split) {
+    const int rc = p->split_inverse(dS, p->red_W, N_G, p->red_fail, st);
+    if (rc) return rc;
+  } else {
+    HS_CUDA_TRY(hs_launch_tri_inverse(dS, p->red_W, N_G, p->red_fail, st));
+  }
   HS_CUDA_TRY(cudaEventRecord(p->red_ev[2], st));
   if (split) {
     // B = W^H; H completed from its lower triangle; then H <- B^H H B on the tensor cores
-    HS_CUDA_TRY(hs_launch_ctrans(p->red_W, N_G, p->red_P, st));
+    HS_CUDA_TRY(hs_launch_ctrans(p->red_W, N_G, N_G, N_G, p->red_P, N_G, st));
     HS_CUDA_TRY(hs_launch_mirror(dH, N_G, N_G, st));
     const int rc = p->split_reduce_transform(p->red_P, dH, N_G, st, p->red_ev[3]);
     if (rc) return rc;

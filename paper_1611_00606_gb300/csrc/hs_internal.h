@@ -71,8 +71,22 @@ cudaError_t hs_launch_reduce_g(const double2* P, const double2* W, double2* H, i
                                const int* fail, cudaStream_t st);
 // H <- H + H^H (diagonal exactly real).
 cudaError_t hs_launch_hermsum(double2* H, int n, const int* fail, cudaStream_t st);
-// B <- A^H (n x n).
-cudaError_t hs_launch_ctrans(const double2* A, int n, double2* B, cudaStream_t st);
+// B (cols x rows, ldb) <- A^H (A rows x cols, lda).
+cudaError_t hs_launch_ctrans(const double2* A, int lda, int rows, int cols, double2* B, int ldb,
+                            cudaStream_t st);
+// C -= T over m x nc (lower != 0: only r >= c).
+cudaError_t hs_launch_sub(double2* C, int ldc, const double2* T, int ldt, int m, int nc, int lower,
+                          const int* fail, cudaStream_t st);
+// Pieces of the blocked Cholesky and inverse (the split form updates the trailing parts
+// on the tensor cores between them): FP64 factorisation of the panel S[j0 :, j0 : j0 + pw)
+// with updates inside the panel; strict upper triangle zeroed; W = I; FP64 block row
+// [i0, i0 + pw) of L W = I with updates inside the block row.
+cudaError_t hs_launch_cholesky_panel(double2* S, int n, int j0, int pw, int* fail,
+                                     cudaStream_t st);
+cudaError_t hs_launch_zero_upper(double2* S, int n, const int* fail, cudaStream_t st);
+cudaError_t hs_launch_eye(double2* W, int n, const int* fail, cudaStream_t st);
+cudaError_t hs_launch_inverse_blockrow(const double2* L, double2* W, int n, int i0, int pw,
+                                       const int* fail, cudaStream_t st);
 
 // ---- real-symmetric variant helpers (k_real.cu) --------------------------------
 // y[i] = (x[i], 0) for i < n.

@@ -84,91 +84,97 @@ __global__ void __launch_bounds__(kThreads) k_potrf_diag(double2* __restrict__ S
 }
 
 // Panel below a factored diagonal block: X <- X L_jj^{-H} for rows [r0, r0 + nrows)
-// of columns [j0, j0 + jb), 64 rows per CTA.  Column c of X L_jj^H = B reads
-// sum_{k <= c} X[r, k] conj(L[c, k]) = B[r, c]: solved left to right.
-__global__ void __launch_bounds__(kThreads) k_trsm_rpanel(double2* __restrict__ S, int ld, int j0,
-                                                          int jb, int r0, int nrows,
-                                                          const int* __restrict__ fail) {
+// of columns [j0, j0 + jb), RPR rows per CTA (small CTAs: the panels are narrow, and
+// FP64 issues slowly, so the rows are spread over as many SMs as possible).  Column
+// c of X L_jj^H = B reads sum_{k <= c} X[r, k] conj(L[c, k]) = B[r, c]: solved left
+// to right.
+constexpr int RPR = 16;
+constexpr int kSmallThreads = 128;
+__global__ void __launch_bounds__(kSmallThreads) k_trsm_rpanel(double2* __restrict__ S, int ld,
+                                                               int j0, int jb, int r0, int nrows,
+                                                               const int* __restrict__ fail) {
   extern __shared__ double2 sm[];
   double2* Lb = sm;            // NB x NB column-major: L[r][c] at c * NB + r
-  double2* x = sm + NB * NB;   // 64 rows x NB columns, column-major: x[c * 64 + r]
+  double2* x = sm + NB * NB;   // RPR rows x NB columns, column-major: x[c * RPR + r]
   if (*fail) return;
   const int tid = threadIdx.x;
-  const int rb = r0 + blockIdx.x * 64;
-  const int nr = min(64, r0 + nrows - rb);
-  for (int e = tid; e < NB * NB; e += kThreads) {
+  const int rb = r0 + blockIdx.x * RPR;
+  const int nr = min(RPR, r0 + nrows - rb);
+  for (int e = tid; e < NB * NB; e += kSmallThreads) {
     const int r = e % NB, c = e / NB;
     Lb[e] = (r < jb && c < jb && r >= c) ? S[(size_t)(j0 + r) + (size_t)(j0 + c) * ld]
                                          : make_double2(0.0, 0.0);
   }
-  for (int e = tid; e < 64 * NB; e += kThreads) {
-    const int r = e % 64, c = e / 64;
+  for (int e = tid; e < RPR * NB; e += kSmallThreads) {
+    const int r = e % RPR, c = e / RPR;
     x[e] = (r < nr && c < jb) ? S[(size_t)(rb + r) + (size_t)(j0 + c) * ld]
                               : make_double2(0.0, 0.0);
   }
   for (int c = 0; c < jb; ++c) {
     __syncthreads();
-    if (tid < 64) {
+    if (tid < RPR) {
       const double rl = 1.0 / Lb[c * NB + c].x;
-      x[c * 64 + tid].x *= rl;
-      x[c * 64 + tid].y *= rl;
+      x[c * RPR + tid].x *= rl;
+      x[c * RPR + tid].y *= rl;
     }
     __syncthreads();
     const int m = jb - c - 1;
-    for (int e = tid; e < 64 * m; e += kThreads) {
-      const int r = e & 63, cc = c + 1 + (e >> 6);
-      x[cc * 64 + r] = zsub(x[cc * 64 + r], zmul(x[c * 64 + r], zconj(Lb[c * NB + cc])));
+    for (int e = tid; e < RPR * m; e += kSmallThreads) {
+      const int r = e % RPR, cc = c + 1 + e / RPR;
+      x[cc * RPR + r] = zsub(x[cc * RPR + r], zmul(x[c * RPR + r], zconj(Lb[c * NB + cc])));
     }
   }
   __syncthreads();
-  for (int e = tid; e < 64 * NB; e += kThreads) {
-    const int r = e % 64, c = e / 64;
+  for (int e = tid; e < RPR * NB; e += kSmallThreads) {
+    const int r = e % RPR, c = e / RPR;
     if (r < nr && c < jb) S[(size_t)(rb + r) + (size_t)(j0 + c) * ld] = x[e];
   }
 }
 
 // Block row of a forward substitution: X <- L_ii^{-1} X for rows [i0, i0 + ib) and
-// columns [0, ncols) of X, 64 columns per CTA; L_ii = L[i0 : i0 + ib, i0 : i0 + ib]
+// columns [0, ncols) of X, RPR columns per CTA; L_ii = L[i0 : i0 + ib, i0 : i0 + ib]
 // (lower triangle read).
-__global__ void __launch_bounds__(kThreads) k_trsm_ldiag(const double2* __restrict__ L, int ldl,
-                                                         int i0, int ib, double2* __restrict__ X,
-                                                         int ldx, int ncols,
-                                                         const int* __restrict__ fail) {
+__global__ void __launch_bounds__(kSmallThreads) k_trsm_ldiag(const double2* __restrict__ L,
+                                                              int ldl, int i0, int ib,
+                                                              double2* __restrict__ X, int ldx,
+                                                              int ncols,
+                                                              const int* __restrict__ fail) {
   extern __shared__ double2 sm[];
   double2* Lb = sm;            // NB x NB column-major
-  double2* x = sm + NB * NB;   // NB rows x 64 columns, row stride 65: x[r * 65 + col]
+  double2* x = sm + NB * NB;   // NB rows x RPR columns, row stride RPR + 1
+  constexpr int XS = RPR + 1;
   if (*fail) return;
   const int tid = threadIdx.x;
-  const int c0 = blockIdx.x * 64;
-  const int nc = min(64, ncols - c0);
-  for (int e = tid; e < NB * NB; e += kThreads) {
+  const int c0 = blockIdx.x * RPR;
+  const int nc = min(RPR, ncols - c0);
+  for (int e = tid; e < NB * NB; e += kSmallThreads) {
     const int r = e % NB, c = e / NB;
     Lb[e] = (r < ib && c < ib && r >= c) ? L[(size_t)(i0 + r) + (size_t)(i0 + c) * ldl]
                                          : make_double2(0.0, 0.0);
   }
-  for (int e = tid; e < NB * 64; e += kThreads) {
+  for (int e = tid; e < NB * RPR; e += kSmallThreads) {
     const int r = e % NB, col = e / NB;
-    x[r * 65 + col] = (r < ib && col < nc) ? X[(size_t)(i0 + r) + (size_t)(c0 + col) * ldx]
+    x[r * XS + col] = (r < ib && col < nc) ? X[(size_t)(i0 + r) + (size_t)(c0 + col) * ldx]
                                            : make_double2(0.0, 0.0);
   }
   for (int k = 0; k < ib; ++k) {
     __syncthreads();
-    if (tid < 64) {
+    if (tid < RPR) {
       const double rl = 1.0 / Lb[k * NB + k].x;
-      x[k * 65 + tid].x *= rl;
-      x[k * 65 + tid].y *= rl;
+      x[k * XS + tid].x *= rl;
+      x[k * XS + tid].y *= rl;
     }
     __syncthreads();
     const int m = ib - k - 1;
-    for (int e = tid; e < 64 * m; e += kThreads) {
-      const int col = e & 63, r = k + 1 + (e >> 6);
-      x[r * 65 + col] = zsub(x[r * 65 + col], zmul(Lb[k * NB + r], x[k * 65 + col]));
+    for (int e = tid; e < RPR * m; e += kSmallThreads) {
+      const int col = e % RPR, r = k + 1 + e / RPR;
+      x[r * XS + col] = zsub(x[r * XS + col], zmul(Lb[k * NB + r], x[k * XS + col]));
     }
   }
   __syncthreads();
-  for (int e = tid; e < NB * 64; e += kThreads) {
+  for (int e = tid; e < NB * RPR; e += kSmallThreads) {
     const int r = e % NB, col = e / NB;
-    if (r < ib && col < nc) X[(size_t)(i0 + r) + (size_t)(c0 + col) * ldx] = x[r * 65 + col];
+    if (r < ib && col < nc) X[(size_t)(i0 + r) + (size_t)(c0 + col) * ldx] = x[r * XS + col];
   }
 }
 
@@ -329,19 +335,36 @@ __global__ void k_hermsum(double2* __restrict__ C, int n, int ld, const int* __r
   }
 }
 
-// B = A^H (n x n, leading dimensions n), 32 x 32 blocks through shared memory.
-__global__ void k_ctrans(const double2* __restrict__ A, int n, double2* __restrict__ B) {
+// B = A^H: A is rows x cols (leading dimension lda), B cols x rows (ldb); 32 x 32
+// blocks through shared memory.
+__global__ void k_ctrans(const double2* __restrict__ A, int lda, int rows, int cols,
+                         double2* __restrict__ B, int ldb) {
   __shared__ double2 t[32][33];
   const int bx = blockIdx.x, by = blockIdx.y;    // source block: rows by, columns bx
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   for (int k = ty; k < 32; k += 8) {
     const int i = by * 32 + tx, j = bx * 32 + k;  // t[k][tx] = A(i, j)
-    t[k][tx] = (i < n && j < n) ? A[i + (size_t)j * n] : make_double2(0.0, 0.0);
+    t[k][tx] = (i < rows && j < cols) ? A[i + (size_t)j * lda] : make_double2(0.0, 0.0);
   }
   __syncthreads();
   for (int k = ty; k < 32; k += 8) {
     const int i = bx * 32 + tx, j = by * 32 + k;  // B(i, j) = conj(A(j, i)) = conj(t[tx][k])
-    if (i < n && j < n) B[i + (size_t)j * n] = zconj(t[tx][k]);
+    if (i < cols && j < rows) B[i + (size_t)j * ldb] = zconj(t[tx][k]);
+  }
+}
+
+// C -= T over m x nc (lower: only r >= c), both column-major.
+__global__ void k_sub(double2* __restrict__ C, int ldc, const double2* __restrict__ T, int ldt,
+                      int m, int nc, int lower, const int* __restrict__ fail) {
+  if (*fail) return;
+  const size_t total = (size_t)m * nc;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    if (lower && r < c) continue;
+    double2* p = C + r + (size_t)c * ldc;
+    const double2 t = T[r + (size_t)c * ldt];
+    *p = make_double2(p->x - t.x, p->y - t.y);
   }
 }
 
@@ -371,8 +394,8 @@ ZgemmArgs zargs(const double2* A, int lda, const double2* B, int ldb, double2* C
 }
 
 constexpr size_t kDiagSmem = (size_t)NB * NB * sizeof(double2);                 // 64 KB
-constexpr size_t kPanelSmem = kDiagSmem + (size_t)64 * NB * sizeof(double2);     // 128 KB
-constexpr size_t kLdiagSmem = kDiagSmem + (size_t)NB * 65 * sizeof(double2);     // 129 KB
+constexpr size_t kPanelSmem = kDiagSmem + (size_t)RPR * NB * sizeof(double2);        // 80 KB
+constexpr size_t kLdiagSmem = kDiagSmem + (size_t)NB * (RPR + 1) * sizeof(double2);  // 81 KB
 
 cudaError_t set_smem() {
   static cudaError_t once = []() {
@@ -391,54 +414,75 @@ cudaError_t set_smem() {
 
 }  // namespace
 
-// S <- L (lower; strict upper zeroed), blocked right-looking.
-cudaError_t hs_launch_cholesky(double2* S, int n, int* fail, cudaStream_t st) {
+static int grid_for(size_t total) {
+  const size_t b = (total + kThreads - 1) / kThreads;
+  return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+// FP64 factorisation of the panel S[j0 :, j0 : j0 + pw) in 64-column blocks; each
+// block's trailing update stays inside the panel (the caller updates the rest).
+cudaError_t hs_launch_cholesky_panel(double2* S, int n, int j0, int pw, int* fail,
+                                     cudaStream_t st) {
   cudaError_t e = set_smem();
   if (e != cudaSuccess) return e;
-  for (int j0 = 0; j0 < n; j0 += NB) {
-    const int jb = n - j0 < NB ? n - j0 : NB;
-    k_potrf_diag<<<1, kThreads, kDiagSmem, st>>>(S, n, j0, jb, fail);
-    const int r0 = j0 + jb, rest = n - r0;
+  for (int jj = j0; jj < j0 + pw; jj += NB) {
+    const int jb = j0 + pw - jj < NB ? j0 + pw - jj : NB;
+    k_potrf_diag<<<1, kThreads, kDiagSmem, st>>>(S, n, jj, jb, fail);
+    const int r0 = jj + jb, rest = n - r0;
     if (rest > 0) {
-      k_trsm_rpanel<<<(rest + 63) / 64, kThreads, kPanelSmem, st>>>(S, n, j0, jb, r0, rest, fail);
-      // trailing lower triangle: S22 -= L21 L21^H
-      const double2* L21 = S + (size_t)r0 + (size_t)j0 * n;
-      ZgemmArgs g = zargs(L21, n, L21, n, S + (size_t)r0 + (size_t)r0 * n, n, rest, rest, jb,
-                          -1.0, 1, fail);
-      g.conjB = 1;
-      g.lower = 1;
-      e = zgemm(g, st);
-      if (e != cudaSuccess) return e;
+      k_trsm_rpanel<<<(rest + RPR - 1) / RPR, kSmallThreads, kPanelSmem, st>>>(S, n, jj, jb, r0,
+                                                                               rest, fail);
+      const int ncol = j0 + pw - r0;  // panel columns right of this block
+      if (ncol > 0) {
+        // S[r0 :, r0 : j0 + pw) lower tiles -= L21 L21^H (rows r0.. x the first ncol of them)
+        const double2* L21 = S + (size_t)r0 + (size_t)jj * n;
+        ZgemmArgs g = zargs(L21, n, L21, n, S + (size_t)r0 + (size_t)r0 * n, n, rest, ncol, jb,
+                            -1.0, 1, fail);
+        g.conjB = 1;
+        g.lower = 1;
+        e = zgemm(g, st);
+        if (e != cudaSuccess) return e;
+      }
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const int blocks = (int)(((size_t)n * n + kThreads - 1) / kThreads) < 4096
-                         ? (int)(((size_t)n * n + kThreads - 1) / kThreads)
-                         : 4096;
-  k_zero_upper<<<blocks, kThreads, 0, st>>>(S, n, n, fail);
+  return cudaSuccess;
+}
+
+cudaError_t hs_launch_zero_upper(double2* S, int n, const int* fail, cudaStream_t st) {
+  k_zero_upper<<<grid_for((size_t)n * n), kThreads, 0, st>>>(S, n, n, fail);
   return cudaGetLastError();
 }
 
-// W <- L^{-1} (lower triangular; L = the factor in S), blocked forward substitution
-// on the identity: block row i of the solution has nonzero columns [0, i0 + ib).
-cudaError_t hs_launch_tri_inverse(const double2* L, double2* W, int n, const int* fail,
-                                  cudaStream_t st) {
+// S <- L (lower; strict upper zeroed), blocked right-looking: one panel of width n.
+cudaError_t hs_launch_cholesky(double2* S, int n, int* fail, cudaStream_t st) {
+  cudaError_t e = hs_launch_cholesky_panel(S, n, 0, n, fail, st);
+  if (e != cudaSuccess) return e;
+  return hs_launch_zero_upper(S, n, fail, st);
+}
+
+cudaError_t hs_launch_eye(double2* W, int n, const int* fail, cudaStream_t st) {
+  k_eye<<<grid_for((size_t)n * n), kThreads, 0, st>>>(W, n, fail);
+  return cudaGetLastError();
+}
+
+// FP64 block row [i0, i0 + pw) of the forward substitution L W = I, in 64-row blocks:
+// block ii's solution has nonzero columns [0, ii + ib); its update of the rows below
+// stays inside the block row (the caller updates the rest).
+cudaError_t hs_launch_inverse_blockrow(const double2* L, double2* W, int n, int i0, int pw,
+                                       const int* fail, cudaStream_t st) {
   cudaError_t e = set_smem();
   if (e != cudaSuccess) return e;
-  const int blocks = (int)(((size_t)n * n + kThreads - 1) / kThreads) < 4096
-                         ? (int)(((size_t)n * n + kThreads - 1) / kThreads)
-                         : 4096;
-  k_eye<<<blocks, kThreads, 0, st>>>(W, n, fail);
-  for (int i0 = 0; i0 < n; i0 += NB) {
-    const int ib = n - i0 < NB ? n - i0 : NB;
-    const int ncols = i0 + ib;
-    k_trsm_ldiag<<<(ncols + 63) / 64, kThreads, kLdiagSmem, st>>>(L, n, i0, ib, W + 0, n, ncols,
-                                                                  fail);
-    const int r0 = i0 + ib, rest = n - r0;
+  for (int ii = i0; ii < i0 + pw; ii += NB) {
+    const int ib = i0 + pw - ii < NB ? i0 + pw - ii : NB;
+    const int ncols = ii + ib;
+    k_trsm_ldiag<<<(ncols + RPR - 1) / RPR, kSmallThreads, kLdiagSmem, st>>>(L, n, ii, ib, W, n,
+                                                                             ncols, fail);
+    const int r0 = ii + ib, rest = i0 + pw - r0;
     if (rest > 0) {
-      // W[r0:, 0:ncols] -= L[r0:, i0:i0+ib] W[i0:i0+ib, 0:ncols]
-      ZgemmArgs g = zargs(L + (size_t)r0 + (size_t)i0 * n, n, W + (size_t)i0, n, W + (size_t)r0,
+      // W[r0 : i0 + pw, 0 : ncols] -= L[r0 :, ii : ii + ib] W[ii : ii + ib, 0 : ncols]
+      ZgemmArgs g = zargs(L + (size_t)r0 + (size_t)ii * n, n, W + (size_t)ii, n, W + (size_t)r0,
                           n, rest, ncols, ib, -1.0, 1, fail);
       e = zgemm(g, st);
       if (e != cudaSuccess) return e;
@@ -447,6 +491,14 @@ cudaError_t hs_launch_tri_inverse(const double2* L, double2* W, int n, const int
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// W <- L^{-1} (lower triangular; L = the factor in S): one block row of height n.
+cudaError_t hs_launch_tri_inverse(const double2* L, double2* W, int n, const int* fail,
+                                  cudaStream_t st) {
+  cudaError_t e = hs_launch_eye(W, n, fail, st);
+  if (e != cudaSuccess) return e;
+  return hs_launch_inverse_blockrow(L, W, n, 0, n, fail, st);
 }
 
 // P <- W tril_h(H) (lower triangular; only tiles on or below the diagonal are written).
@@ -469,9 +521,18 @@ cudaError_t hs_launch_reduce_g(const double2* P, const double2* W, double2* H, i
   return zgemm(g, st);
 }
 
-cudaError_t hs_launch_ctrans(const double2* A, int n, double2* B, cudaStream_t st) {
-  const int nb = (n + 31) / 32;
-  k_ctrans<<<dim3(nb, nb), dim3(32, 8), 0, st>>>(A, n, B);
+cudaError_t hs_launch_ctrans(const double2* A, int lda, int rows, int cols, double2* B, int ldb,
+                            cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  k_ctrans<<<dim3((cols + 31) / 32, (rows + 31) / 32), dim3(32, 8), 0, st>>>(A, lda, rows, cols,
+                                                                              B, ldb);
+  return cudaGetLastError();
+}
+
+cudaError_t hs_launch_sub(double2* C, int ldc, const double2* T, int ldt, int m, int nc, int lower,
+                          const int* fail, cudaStream_t st) {
+  if (m <= 0 || nc <= 0) return cudaSuccess;
+  k_sub<<<grid_for((size_t)m * nc), kThreads, 0, st>>>(C, ldc, T, ldt, m, nc, lower, fail);
   return cudaGetLastError();
 }
 

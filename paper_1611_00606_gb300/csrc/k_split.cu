@@ -2034,3 +2034,138 @@ int hs_plan_s::split_reduce_transform(const double2* B, double2* H, int n, cudaS
   if (rc) return rc;
   return hs_launch_mirror(H, n, n, st) == cudaSuccess ? HS_OK : HS_ECUDA;
 }
+
+// ---------------------------------------------------------------------------
+// General products on the slice path for the blocked Cholesky and inverse of hs_reduce.
+// Operands are K-major (K complex rows x columns, column-major); red_M holds their
+// slices (its capacity, sized for the two-sided transform, covers K <= kRedPanel and
+// up to n_pad + n columns).
+
+// out = lower(X^H X) (nc x nc, leading dimension nc; whole lower tiles written).
+int hs_plan_s::split_herk_lower(const double2* X, int ldX, int K, int nc, double2* out,
+                                cudaStream_t st) {
+  const int s = slices, rp = rows_pad_of(nc), NKB = kpad_of(K, 1) / KB;
+  int n_stage;
+  size_t smem;
+  int rc = split_geometry(n_stage, smem);
+  if (rc) return rc;
+  SliceParams sp{};
+  sp.job[0] = SliceJob{X, nullptr, red_M.plain, red_M.rot, red_M.expo, ldX, K};
+  rc = slice_launch(sp, 1, s, nc, rp, 1, false, st);
+  if (rc) return rc;
+  SplitParams* PP = new (std::nothrow) SplitParams;
+  if (!PP) return HS_ENOMEM;
+  std::unique_ptr<SplitParams> own(PP);
+  SplitParams& P = *PP;
+  std::memset(&P, 0, sizeof(P));
+  if (!encode_tiles(&P.maps[0], red_M.plain, NKB, rp / 64, s) ||
+      !encode_tiles(&P.maps[1], red_M.rot, NKB, rp / 64, s))
+    return HS_ECUDA;
+  P.seg[0] = SplitSeg{0, 0, 1, NKB, red_M.expo, red_M.expo};
+  P.nseg = 1;
+  P.s = s;
+  P.N_G = nc;
+  P.ldC = nc;
+  P.nbj = (nc + BNC - 1) / BNC;
+  P.rows_pad = rp;
+  P.err = err_d;
+  P.bi0 = 0;
+  P.nbi = (nc + BM - 1) / BM;
+  P.band = contract_band();
+  P.ntiles = contract_tiles(P);
+  P.C = out;
+  P.n_stage = n_stage;
+  return launch_gemm(MODE_CONTRACT, s, P.ntiles, smem, st, P);
+}
+
+// out = A^H B (m x nc) for A (K x m) and B (K x nc): the block below the split of
+// lower(M^H M) for M = [B | 0 | A] (zeros from column nc up to nc_pad); out is
+// m x (nc_pad + m) with leading dimension m, the product in its first nc columns.
+int hs_plan_s::split_gemm_ahb(const double2* A, int ldA, int m, const double2* B, int ldB, int nc,
+                              int K, double2* out, cudaStream_t st) {
+  const int s = slices, nc_pad = rows_pad_of(nc), NM = nc_pad + m, rpM = rows_pad_of(NM);
+  const int NKB = kpad_of(K, 1) / KB;
+  int n_stage;
+  size_t smem;
+  int rc = split_geometry(n_stage, smem);
+  if (rc) return rc;
+  SliceParams sp{};
+  sp.job[0] = SliceJob{B, nullptr, red_M.plain, red_M.rot, red_M.expo, ldB, K};
+  rc = slice_launch(sp, 1, s, nc, rpM, 1, false, st, 0, nc_pad);
+  if (rc) return rc;
+  SliceParams sq{};
+  const double2* As =
+      (const double2*)((uintptr_t)A - (uintptr_t)nc_pad * (uintptr_t)ldA * sizeof(double2));
+  sq.job[0] = SliceJob{As, nullptr, red_M.plain, red_M.rot, red_M.expo, ldA, K};
+  rc = slice_launch(sq, 1, s, NM, rpM, 1, false, st, nc_pad, -1);
+  if (rc) return rc;
+  SplitParams* PP = new (std::nothrow) SplitParams;
+  if (!PP) return HS_ENOMEM;
+  std::unique_ptr<SplitParams> own(PP);
+  SplitParams& P = *PP;
+  std::memset(&P, 0, sizeof(P));
+  if (!encode_tiles(&P.maps[0], red_M.plain, NKB, rpM / 64, s) ||
+      !encode_tiles(&P.maps[1], red_M.rot, NKB, rpM / 64, s))
+    return HS_ECUDA;
+  P.seg[0] = SplitSeg{0, 0, 1, NKB, red_M.expo, red_M.expo};
+  P.nseg = 1;
+  P.s = s;
+  P.N_G = NM;
+  P.ldC = m;
+  P.nbj = (NM + BNC - 1) / BNC;
+  P.rows_pad = rpM;
+  P.err = err_d;
+  P.bi0 = nc_pad / BM;
+  P.nbi = (NM + BM - 1) / BM;
+  P.band = contract_band();
+  P.ntiles = contract_tiles(P);
+  P.C = (double2*)((uintptr_t)out - (uintptr_t)nc_pad * sizeof(double2));  // row nc_pad -> 0
+  P.n_stage = n_stage;
+  return launch_gemm(MODE_CONTRACT, s, P.ntiles, smem, st, P);
+}
+
+// Right-looking Cholesky in panels of kRedPanel columns: each panel in FP64, then
+// S22 -= L21 L21^H = lower(X^H X) with X = L21^H on the slice path.
+int hs_plan_s::split_cholesky(double2* S, int n, int* fail, cudaStream_t st) {
+  int rc = split_reduce_alloc(n);
+  if (rc) return rc;
+  for (int j0 = 0; j0 < n; j0 += kRedPanel) {
+    const int pw = std::min(kRedPanel, n - j0);
+    if (hs_launch_cholesky_panel(S, n, j0, pw, fail, st) != cudaSuccess) return HS_ECUDA;
+    const int r0 = j0 + pw, n2 = n - r0;
+    if (n2 <= 0) break;
+    double2* X = red_P;  // pw x n2, leading dimension pw
+    if (hs_launch_ctrans(S + (size_t)r0 + (size_t)j0 * n, n, n2, pw, X, pw, st) != cudaSuccess)
+      return HS_ECUDA;
+    rc = split_herk_lower(X, pw, pw, n2, red_Z, st);
+    if (rc) return rc;
+    if (hs_launch_sub(S + (size_t)r0 + (size_t)r0 * n, n, red_Z, n2, n2, n2, 1, fail, st) !=
+        cudaSuccess)
+      return HS_ECUDA;
+  }
+  return hs_launch_zero_upper(S, n, fail, st) == cudaSuccess ? HS_OK : HS_ECUDA;
+}
+
+// Forward substitution L W = I in block rows of kRedPanel: each block row in FP64,
+// then W[r0 :, 0 : ncols] -= L[r0 :, i0 : i0 + pw] W[i0 : i0 + pw, 0 : ncols] on the
+// slice path (A = that block of L, conjugate-transposed to K-major).
+int hs_plan_s::split_inverse(const double2* L, double2* W, int n, const int* fail,
+                             cudaStream_t st) {
+  int rc = split_reduce_alloc(n);
+  if (rc) return rc;
+  if (hs_launch_eye(W, n, fail, st) != cudaSuccess) return HS_ECUDA;
+  for (int i0 = 0; i0 < n; i0 += kRedPanel) {
+    const int pw = std::min(kRedPanel, n - i0);
+    if (hs_launch_inverse_blockrow(L, W, n, i0, pw, fail, st) != cudaSuccess) return HS_ECUDA;
+    const int r0 = i0 + pw, m = n - r0, ncols = i0 + pw;
+    if (m <= 0) break;
+    double2* A = red_P;  // pw x m, leading dimension pw
+    if (hs_launch_ctrans(L + (size_t)r0 + (size_t)i0 * n, n, m, pw, A, pw, st) != cudaSuccess)
+      return HS_ECUDA;
+    rc = split_gemm_ahb(A, pw, m, W + i0, n, ncols, pw, red_Z, st);
+    if (rc) return rc;
+    if (hs_launch_sub(W + r0, n, red_Z, m, m, ncols, 0, fail, st) != cudaSuccess)
+      return HS_ECUDA;
+  }
+  return HS_OK;
+}

@@ -16,6 +16,7 @@
 constexpr int kMaxNL = 168;       // packed lower triangle of T^AA fits in 227 KB smem
 constexpr int kDefaultSlices = 5;
 constexpr int kMaxSlices = 7;  // 7 + 9*(s-1) bits must fit an int64 digit word
+constexpr int kRedPanel = 256;  // hs_reduce, split plans: FP64 panel width
 
 // Slice buffers of one operand source: s BF16 arrays [p][rows_pad][kpad] of
 // (re, im) pairs, optionally the same for (im, -re) pairs, and one exponent
@@ -156,6 +157,14 @@ struct hs_plan_s {
                              cudaEvent_t mid);
   int split_reduce_alloc(int n);
   void split_reduce_release();
+  // the Cholesky and the inverse of hs_reduce on split plans: FP64 panels of kRedPanel
+  // columns (rows), trailing updates as slice contractions (red_M, red_Z, red_P as scratch)
+  int split_cholesky(double2* S, int n, int* fail, cudaStream_t st);
+  int split_inverse(const double2* L, double2* W, int n, const int* fail, cudaStream_t st);
+  // lower(X^H X) and A^H B for K-major operands on the slice path (scratch: red_M)
+  int split_herk_lower(const double2* X, int ldX, int K, int nc, double2* out, cudaStream_t st);
+  int split_gemm_ahb(const double2* A, int ldA, int m, const double2* B, int ldB, int nc, int K,
+                     double2* out, cudaStream_t st);
   int check_device_error();
   void fill_info(hs_info* info, bool factored);
   bool serve_busy();

@@ -6,12 +6,13 @@ Cholesky and of triangular solves is bounded by n u kappa(S) relative to the
 result (u = 2^-53), so every comparison uses max(1e-13, n u kappa(S)) with kappa
 the 2-norm condition number of the case's S.
 
-Split form (plans of precision split_bf16): the Cholesky and the inverse are the
-same FP64 kernels (L is bitwise equal to the FP64 form's), the two products
-H L^{-H} and Z^H B + B^H Z run on the BF16 slice path, whose results carry a
-relative error of at most the split assembly's 1e-10 of their operands' scale;
-||B||^2 = 1/lambda_min(S) and ||C|| >= ||H|| / lambda_max(S) turn that into
-1e-10 kappa(S) relative to C.
+Split form (plans of precision split_bf16): the Cholesky and the inverse factor
+256-wide panels in FP64 (up to N_G = 256 L is bitwise equal to the FP64 form's)
+and run their trailing updates, and the two products H L^{-H} and Z^H B + B^H Z,
+on the BF16 slice path, whose results carry a relative error of at most the split
+assembly's 1e-10 of their operands' scale; ||B||^2 = 1/lambda_min(S) and
+||C|| >= ||H|| / lambda_max(S) turn that into 1e-10 kappa(S) relative to C, and
+the Schur complements' errors into no more than that relative to L.
 
 Both forms: L's strict upper triangle is exactly zero, and C exactly Hermitian
 with an exactly real diagonal.
@@ -71,7 +72,7 @@ def _check(C, L, H, S, precision="fp64"):
     assert fail == 0
     tol = _tol(S, precision)
     assert np.all(np.triu(L, 1) == 0)
-    assert rel_frobenius(L, Lr) <= _tol(S), (rel_frobenius(L, Lr), _tol(S))
+    assert rel_frobenius(L, Lr) <= tol, (rel_frobenius(L, Lr), tol)
     assert rel_frobenius(C, Cr) <= tol, (rel_frobenius(C, Cr), tol)
     assert np.array_equal(C, C.conj().T)
     assert np.all(np.diag(C).imag == 0)
@@ -99,17 +100,20 @@ def test_reduce_parity(hs, n, cond):
     (1, 1.0),
     (65, 1e3),
     (130, 1e4),
-    (257, 1e3),      # several row blocks of the stacked operand, ragged
-    (520, 1e6),
+    (256, 1e3),      # one FP64 panel exactly
+    (257, 1e3),      # a 1-wide second panel; several row blocks of the stacked operand
+    (520, 1e6),      # three panels, ragged, ill-conditioned
+    (777, 1e2),      # four panels: trailing updates of several sizes
 ])
 def test_reduce_split_parity(hs, n, cond):
     H, S = synth.reduce_inputs(n, seed=n + 7, cond=cond)
     C, L, info = _reduce(hs, H, S, "split_bf16")
     C64, L64, _ = _reduce(hs, H, S, "fp64")
-    assert np.array_equal(L, L64)  # the factor is FP64 in both forms
+    if n <= 256:
+        assert np.array_equal(L, L64)  # one panel: the factor is all FP64
     eL, eC = _check(C, L, H, S, "split_bf16")
-    print(f"split n={n} cond={cond:g}: C {eC:.2e} (fp64 form {rel_frobenius(C64, C):.2e} apart) "
-          f"ms {info['ms_total']:.3f}")
+    print(f"split n={n} cond={cond:g}: L {eL:.2e} C {eC:.2e} (fp64 form {rel_frobenius(C64, C):.2e} "
+          f"apart) ms {info['ms_total']:.3f}")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
@@ -176,9 +180,8 @@ def test_reduce_paper_scale(hs):
     with hs.Plan(1, 1, w.N_G, "fp64") as p:
         info64 = p.reduce(H0d, S0d)
     C64, L64 = H0d.cpu().numpy(), S0d.cpu().numpy()
-    assert np.array_equal(L, L64)
     eL64, eC64 = _check(C64, L64, H0, S0)
-    print(f"auag_like_4000: split C {eC:.2e} ms {info['ms_total']:.1f}; "
+    print(f"auag_like_4000: split L {eL:.2e} C {eC:.2e} ms {info['ms_total']:.1f}; "
           f"fp64 L {eL64:.2e} C {eC64:.2e} ms {info64['ms_total']:.1f}")
 
 
