@@ -255,7 +255,7 @@ def run_real(args, w):
 
 def _reduce_launches(n: int, split: bool) -> int:
     """Kernel launches of one hs_reduce call (the library's launch sequence)."""
-    pw_max = 256 if split else n
+    pw_max = 128 if split else n
     cnt = 0
     for j0 in range(0, n, pw_max):  # Cholesky panels: diagonal blocks, panels, updates
         pw = min(pw_max, n - j0)

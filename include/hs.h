@@ -213,7 +213,7 @@ int hs_assemble_static(const hs_z* A, const hs_z* B, const hs_z* T_AA, const hs_
  * diagonal as its real part).  HS_FP64 plans: FP64 (DFMA) throughout, blocked
  * Cholesky, triangular inverse W = L^{-1} and the products C = G + G^H with
  * G = W tril(H) W^H.  HS_SPLIT_BF16 plans: the Cholesky and the inverse factor
- * 256-wide panels in FP64 and run their trailing updates, and the two-sided products
+ * 128-wide panels in FP64 and run their trailing updates, and the two-sided products
  * (H L^{-H}, then C = Z^H B + B^H Z with B = L^{-H} and Z = H B / 2), as BF16 slice
  * contractions on the tensor cores with the plan's slice count; relative error about
  * 1e-10 kappa(S) instead of FP64's.  Complex plans

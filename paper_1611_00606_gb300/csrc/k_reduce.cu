@@ -25,12 +25,20 @@ constexpr int RT = 64;   // output tile of k_zgemm (rows and columns)
 constexpr int RK = 16;   // K step of k_zgemm
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
 __device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
-__device__ __forceinline__ double2 zsub(double2 a, double2 b) {
-  return make_double2(a.x - b.x, a.y - b.y);
+// acc -= a conj(b)
+__device__ __forceinline__ void zfms_conj(double2& acc, double2 a, double2 b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(-a.y, b.x, acc.y);
+  acc.y = fma(a.x, b.y, acc.y);
+}
+// acc -= a b
+__device__ __forceinline__ void zfms(double2& acc, double2 a, double2 b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
 }
 // acc += a b
 __device__ __forceinline__ void zfma(double2& acc, double2 a, double2 b) {
@@ -70,10 +78,11 @@ __global__ void __launch_bounds__(kThreads) k_potrf_diag(double2* __restrict__ S
     }
     __syncthreads();
     if (tid == 0) a[k * NB + k] = make_double2(l, 0.0);
-    const int m = jb - k - 1;
-    for (int e = tid; e < m * m; e += kThreads) {
-      const int r = k + 1 + e % m, c = k + 1 + e / m;
-      if (r >= c) a[c * NB + r] = zsub(a[c * NB + r], zmul(a[k * NB + r], zconj(a[k * NB + c])));
+    // trailing lower triangle: 16 x 16 threads over (row, column) pairs
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int c = k + 1 + ty; c < jb; c += 16) {
+      const double2 lc = a[k * NB + c];
+      for (int r = c + tx; r < jb; r += 16) zfms_conj(a[c * NB + r], a[k * NB + r], lc);
     }
   }
   __syncthreads();
@@ -121,7 +130,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_trsm_rpanel(double2* __restri
     const int m = jb - c - 1;
     for (int e = tid; e < RPR * m; e += kSmallThreads) {
       const int r = e % RPR, cc = c + 1 + e / RPR;
-      x[cc * RPR + r] = zsub(x[cc * RPR + r], zmul(x[c * RPR + r], zconj(Lb[c * NB + cc])));
+      zfms_conj(x[cc * RPR + r], x[c * RPR + r], Lb[c * NB + cc]);
     }
   }
   __syncthreads();
@@ -168,7 +177,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_trsm_ldiag(const double2* __r
     const int m = ib - k - 1;
     for (int e = tid; e < RPR * m; e += kSmallThreads) {
       const int col = e % RPR, r = k + 1 + e / RPR;
-      x[r * XS + col] = zsub(x[r * XS + col], zmul(Lb[k * NB + r], x[k * XS + col]));
+      zfms(x[r * XS + col], Lb[k * NB + r], x[k * XS + col]);
     }
   }
   __syncthreads();

@@ -16,7 +16,7 @@
 constexpr int kMaxNL = 168;       // packed lower triangle of T^AA fits in 227 KB smem
 constexpr int kDefaultSlices = 5;
 constexpr int kMaxSlices = 7;  // 7 + 9*(s-1) bits must fit an int64 digit word
-constexpr int kRedPanel = 256;  // hs_reduce, split plans: FP64 panel width
+constexpr int kRedPanel = 128;  // hs_reduce, split plans: FP64 panel width
 
 // Slice buffers of one operand source: s BF16 arrays [p][rows_pad][kpad] of
 // (re, im) pairs, optionally the same for (im, -re) pairs, and one exponent

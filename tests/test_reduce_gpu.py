@@ -7,7 +7,7 @@ result (u = 2^-53), so every comparison uses max(1e-13, n u kappa(S)) with kappa
 the 2-norm condition number of the case's S.
 
 Split form (plans of precision split_bf16): the Cholesky and the inverse factor
-256-wide panels in FP64 (up to N_G = 256 L is bitwise equal to the FP64 form's)
+128-wide panels in FP64 (up to N_G = 128 L is bitwise equal to the FP64 form's)
 and run their trailing updates, and the two products H L^{-H} and Z^H B + B^H Z,
 on the BF16 slice path, whose results carry a relative error of at most the split
 assembly's 1e-10 of their operands' scale; ||B||^2 = 1/lambda_min(S) and
@@ -100,8 +100,9 @@ def test_reduce_parity(hs, n, cond):
     (1, 1.0),
     (65, 1e3),
     (130, 1e4),
-    (256, 1e3),      # one FP64 panel exactly
-    (257, 1e3),      # a 1-wide second panel; several row blocks of the stacked operand
+    (128, 1e3),      # one FP64 panel exactly
+    (129, 1e3),      # a 1-wide second panel
+    (257, 1e3),      # three panels, the last 1 wide; several row blocks of the stacked operand
     (520, 1e6),      # three panels, ragged, ill-conditioned
     (777, 1e2),      # four panels: trailing updates of several sizes
 ])
@@ -109,7 +110,7 @@ def test_reduce_split_parity(hs, n, cond):
     H, S = synth.reduce_inputs(n, seed=n + 7, cond=cond)
     C, L, info = _reduce(hs, H, S, "split_bf16")
     C64, L64, _ = _reduce(hs, H, S, "fp64")
-    if n <= 256:
+    if n <= 128:
         assert np.array_equal(L, L64)  # one panel: the factor is all FP64
     eL, eC = _check(C, L, H, S, "split_bf16")
     print(f"split n={n} cond={cond:g}: L {eL:.2e} C {eC:.2e} (fp64 form {rel_frobenius(C64, C):.2e} "
