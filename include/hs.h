@@ -229,7 +229,8 @@ typedef struct {
   int fail_col;          /* 0, or the failing column of the Cholesky (1-based) */
   double ms_total;       /* device time of the call (CUDA events) */
   double ms_cholesky;    /* S = L L^H */
-  double ms_inverse;     /* W = L^{-1} */
+  double ms_inverse;     /* W = L^{-1} (split plans: the part not overlapped with the
+                            Cholesky, which it follows panel by panel on another stream) */
   double ms_p;           /* P = W tril_h(H) (tril_h: lower triangle, diagonal halved) */
   double ms_g;           /* G = P W^H and C = G + G^H */
 } hs_reduce_info;

@@ -619,24 +619,30 @@ extern "C" int hs_reduce(hs_plan_t p, hs_z* H, hs_z* S, int N_G, hs_reduce_info*
   HS_CUDA_TRY(cudaMemsetAsync(p->red_fail, 0, sizeof(int), st));
   HS_CUDA_TRY(cudaEventRecord(p->red_ev[0], st));
   if (split) {
-    const int rc = p->split_cholesky(dS, N_G, p->red_fail, st);
+    // the Cholesky on the plan's stream; the inverse on the S stream, block row i as soon
+    // as the Cholesky's panel i is final (both chains are narrow FP64 launches between
+    // tensor-core updates, so they overlap)
+    if (!p->s_stream) HS_CUDA_TRY(cudaStreamCreateWithFlags(&p->s_stream, cudaStreamNonBlocking));
+    cudaStream_t s2 = p->s_stream;
+    HS_CUDA_TRY(cudaEventRecord(p->red_ev[5], st));  // after the failure word's reset
+    HS_CUDA_TRY(cudaStreamWaitEvent(s2, p->red_ev[5], 0));
+    int rc = p->split_cholesky(dS, N_G, p->red_fail, st);
     if (rc) return rc;
-  } else {
-    HS_CUDA_TRY(hs_launch_cholesky(dS, N_G, p->red_fail, st));
-  }
-  HS_CUDA_TRY(cudaEventRecord(p->red_ev[1], st));
-  if (split) {  // the slice path does not read the failure word: stop here if S failed
+    HS_CUDA_TRY(cudaEventRecord(p->red_ev[1], st));
+    rc = p->split_inverse(dS, p->red_W, N_G, p->red_fail, s2);
+    if (rc) return rc;
+    HS_CUDA_TRY(cudaEventRecord(p->red_ev[6], s2));
+    HS_CUDA_TRY(cudaStreamWaitEvent(st, p->red_ev[6], 0));
+    // the slice path does not read the failure word: stop here if S failed
     HS_CUDA_TRY(cudaMemcpyAsync(&fail, p->red_fail, sizeof(int), cudaMemcpyDeviceToHost, st));
     HS_CUDA_TRY(cudaStreamSynchronize(st));
     if (fail) {
       if (info) info->fail_col = fail;
       return HS_ENOTPD;
     }
-  }
-  if (split) {
-    const int rc = p->split_inverse(dS, p->red_W, N_G, p->red_fail, st);
-    if (rc) return rc;
   } else {
+    HS_CUDA_TRY(hs_launch_cholesky(dS, N_G, p->red_fail, st));
+    HS_CUDA_TRY(cudaEventRecord(p->red_ev[1], st));
     HS_CUDA_TRY(hs_launch_tri_inverse(dS, p->red_W, N_G, p->red_fail, st));
   }
   HS_CUDA_TRY(cudaEventRecord(p->red_ev[2], st));

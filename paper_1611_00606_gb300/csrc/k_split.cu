@@ -1897,7 +1897,7 @@ int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const
 // The second contraction reads B's slices as M's first n rows.
 
 void hs_plan_s::split_reduce_release() {
-  for (SliceBuf* b : {&red_M, &red_Zs}) {
+  for (SliceBuf* b : {&red_M, &red_Zs, &red_M2}) {
     if (b->plain) cudaFree(b->plain);
     if (b->rot) cudaFree(b->rot);
     if (b->expo) cudaFree(b->expo);
@@ -1905,8 +1905,13 @@ void hs_plan_s::split_reduce_release() {
   }
   if (red_Z) cudaFree(red_Z);
   if (red_half) cudaFree(red_half);
-  red_Z = nullptr;
+  if (red_P2) cudaFree(red_P2);
+  if (red_Z2) cudaFree(red_Z2);
+  red_Z = red_Z2 = red_P2 = nullptr;
   red_half = nullptr;
+  for (cudaEvent_t& e : red_pev)
+    if (e) cudaEventDestroy(e);
+  red_pev.clear();
   red_split_cap = 0;
 }
 
@@ -1926,7 +1931,16 @@ int hs_plan_s::split_reduce_alloc(int n) {
       cudaMalloc((void**)&red_Zs.rot, oneZ) == cudaSuccess &&
       cudaMalloc((void**)&red_Zs.expo, sizeof(int) * rp) == cudaSuccess &&
       cudaMalloc((void**)&red_Z, sizeof(double2) * (size_t)n * NM) == cudaSuccess &&
-      cudaMalloc((void**)&red_half, sizeof(double) * (size_t)n) == cudaSuccess;
+      cudaMalloc((void**)&red_half, sizeof(double) * (size_t)n) == cudaSuccess &&
+      // the inverse's scratch: slices of K <= kRedPanel over up to n_pad + n columns,
+      // a kRedPanel x n transposed block, an n x (n_pad + n) product
+      cudaMalloc((void**)&red_M2.plain, (size_t)slices * rpM * kpad_of(kRedPanel, 1) * 2) ==
+          cudaSuccess &&
+      cudaMalloc((void**)&red_M2.rot, (size_t)slices * rpM * kpad_of(kRedPanel, 1) * 2) ==
+          cudaSuccess &&
+      cudaMalloc((void**)&red_M2.expo, sizeof(int) * rpM) == cudaSuccess &&
+      cudaMalloc((void**)&red_P2, sizeof(double2) * (size_t)kRedPanel * n) == cudaSuccess &&
+      cudaMalloc((void**)&red_Z2, sizeof(double2) * (size_t)n * NM) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     split_reduce_release();
@@ -1938,6 +1952,12 @@ int hs_plan_s::split_reduce_alloc(int n) {
     split_reduce_release();
     return HS_ECUDA;
   }
+  red_pev.assign((size_t)(n + kRedPanel - 1) / kRedPanel, nullptr);
+  for (cudaEvent_t& e : red_pev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      split_reduce_release();
+      return HS_ECUDA;
+    }
   red_split_cap = n;
   return HS_OK;
 }
@@ -2043,14 +2063,14 @@ int hs_plan_s::split_reduce_transform(const double2* B, double2* H, int n, cudaS
 
 // out = lower(X^H X) (nc x nc, leading dimension nc; whole lower tiles written).
 int hs_plan_s::split_herk_lower(const double2* X, int ldX, int K, int nc, double2* out,
-                                cudaStream_t st) {
+                                SliceBuf& sb, cudaStream_t st) {
   const int s = slices, rp = rows_pad_of(nc), NKB = kpad_of(K, 1) / KB;
   int n_stage;
   size_t smem;
   int rc = split_geometry(n_stage, smem);
   if (rc) return rc;
   SliceParams sp{};
-  sp.job[0] = SliceJob{X, nullptr, red_M.plain, red_M.rot, red_M.expo, ldX, K};
+  sp.job[0] = SliceJob{X, nullptr, sb.plain, sb.rot, sb.expo, ldX, K};
   rc = slice_launch(sp, 1, s, nc, rp, 1, false, st);
   if (rc) return rc;
   SplitParams* PP = new (std::nothrow) SplitParams;
@@ -2058,10 +2078,10 @@ int hs_plan_s::split_herk_lower(const double2* X, int ldX, int K, int nc, double
   std::unique_ptr<SplitParams> own(PP);
   SplitParams& P = *PP;
   std::memset(&P, 0, sizeof(P));
-  if (!encode_tiles(&P.maps[0], red_M.plain, NKB, rp / 64, s) ||
-      !encode_tiles(&P.maps[1], red_M.rot, NKB, rp / 64, s))
+  if (!encode_tiles(&P.maps[0], sb.plain, NKB, rp / 64, s) ||
+      !encode_tiles(&P.maps[1], sb.rot, NKB, rp / 64, s))
     return HS_ECUDA;
-  P.seg[0] = SplitSeg{0, 0, 1, NKB, red_M.expo, red_M.expo};
+  P.seg[0] = SplitSeg{0, 0, 1, NKB, sb.expo, sb.expo};
   P.nseg = 1;
   P.s = s;
   P.N_G = nc;
@@ -2082,7 +2102,7 @@ int hs_plan_s::split_herk_lower(const double2* X, int ldX, int K, int nc, double
 // lower(M^H M) for M = [B | 0 | A] (zeros from column nc up to nc_pad); out is
 // m x (nc_pad + m) with leading dimension m, the product in its first nc columns.
 int hs_plan_s::split_gemm_ahb(const double2* A, int ldA, int m, const double2* B, int ldB, int nc,
-                              int K, double2* out, cudaStream_t st) {
+                              int K, double2* out, SliceBuf& sb, cudaStream_t st) {
   const int s = slices, nc_pad = rows_pad_of(nc), NM = nc_pad + m, rpM = rows_pad_of(NM);
   const int NKB = kpad_of(K, 1) / KB;
   int n_stage;
@@ -2090,13 +2110,13 @@ int hs_plan_s::split_gemm_ahb(const double2* A, int ldA, int m, const double2* B
   int rc = split_geometry(n_stage, smem);
   if (rc) return rc;
   SliceParams sp{};
-  sp.job[0] = SliceJob{B, nullptr, red_M.plain, red_M.rot, red_M.expo, ldB, K};
+  sp.job[0] = SliceJob{B, nullptr, sb.plain, sb.rot, sb.expo, ldB, K};
   rc = slice_launch(sp, 1, s, nc, rpM, 1, false, st, 0, nc_pad);
   if (rc) return rc;
   SliceParams sq{};
   const double2* As =
       (const double2*)((uintptr_t)A - (uintptr_t)nc_pad * (uintptr_t)ldA * sizeof(double2));
-  sq.job[0] = SliceJob{As, nullptr, red_M.plain, red_M.rot, red_M.expo, ldA, K};
+  sq.job[0] = SliceJob{As, nullptr, sb.plain, sb.rot, sb.expo, ldA, K};
   rc = slice_launch(sq, 1, s, NM, rpM, 1, false, st, nc_pad, -1);
   if (rc) return rc;
   SplitParams* PP = new (std::nothrow) SplitParams;
@@ -2104,10 +2124,10 @@ int hs_plan_s::split_gemm_ahb(const double2* A, int ldA, int m, const double2* B
   std::unique_ptr<SplitParams> own(PP);
   SplitParams& P = *PP;
   std::memset(&P, 0, sizeof(P));
-  if (!encode_tiles(&P.maps[0], red_M.plain, NKB, rpM / 64, s) ||
-      !encode_tiles(&P.maps[1], red_M.rot, NKB, rpM / 64, s))
+  if (!encode_tiles(&P.maps[0], sb.plain, NKB, rpM / 64, s) ||
+      !encode_tiles(&P.maps[1], sb.rot, NKB, rpM / 64, s))
     return HS_ECUDA;
-  P.seg[0] = SplitSeg{0, 0, 1, NKB, red_M.expo, red_M.expo};
+  P.seg[0] = SplitSeg{0, 0, 1, NKB, sb.expo, sb.expo};
   P.nseg = 1;
   P.s = s;
   P.N_G = NM;
@@ -2132,12 +2152,14 @@ int hs_plan_s::split_cholesky(double2* S, int n, int* fail, cudaStream_t st) {
   for (int j0 = 0; j0 < n; j0 += kRedPanel) {
     const int pw = std::min(kRedPanel, n - j0);
     if (hs_launch_cholesky_panel(S, n, j0, pw, fail, st) != cudaSuccess) return HS_ECUDA;
+    // panel j0 / kRedPanel of L is final: later updates touch columns right of it only
+    if (cudaEventRecord(red_pev[j0 / kRedPanel], st) != cudaSuccess) return HS_ECUDA;
     const int r0 = j0 + pw, n2 = n - r0;
     if (n2 <= 0) break;
     double2* X = red_P;  // pw x n2, leading dimension pw
     if (hs_launch_ctrans(S + (size_t)r0 + (size_t)j0 * n, n, n2, pw, X, pw, st) != cudaSuccess)
       return HS_ECUDA;
-    rc = split_herk_lower(X, pw, pw, n2, red_Z, st);
+    rc = split_herk_lower(X, pw, pw, n2, red_Z, red_M, st);
     if (rc) return rc;
     if (hs_launch_sub(S + (size_t)r0 + (size_t)r0 * n, n, red_Z, n2, n2, n2, 1, fail, st) !=
         cudaSuccess)
@@ -2148,7 +2170,8 @@ int hs_plan_s::split_cholesky(double2* S, int n, int* fail, cudaStream_t st) {
 
 // Forward substitution L W = I in block rows of kRedPanel: each block row in FP64,
 // then W[r0 :, 0 : ncols] -= L[r0 :, i0 : i0 + pw] W[i0 : i0 + pw, 0 : ncols] on the
-// slice path (A = that block of L, conjugate-transposed to K-major).
+// slice path (A = that block of L, conjugate-transposed to K-major).  Block row i reads
+// L's panel i only: it starts once split_cholesky has recorded that panel's event.
 int hs_plan_s::split_inverse(const double2* L, double2* W, int n, const int* fail,
                              cudaStream_t st) {
   int rc = split_reduce_alloc(n);
@@ -2156,15 +2179,16 @@ int hs_plan_s::split_inverse(const double2* L, double2* W, int n, const int* fai
   if (hs_launch_eye(W, n, fail, st) != cudaSuccess) return HS_ECUDA;
   for (int i0 = 0; i0 < n; i0 += kRedPanel) {
     const int pw = std::min(kRedPanel, n - i0);
+    if (cudaStreamWaitEvent(st, red_pev[i0 / kRedPanel], 0) != cudaSuccess) return HS_ECUDA;
     if (hs_launch_inverse_blockrow(L, W, n, i0, pw, fail, st) != cudaSuccess) return HS_ECUDA;
     const int r0 = i0 + pw, m = n - r0, ncols = i0 + pw;
     if (m <= 0) break;
-    double2* A = red_P;  // pw x m, leading dimension pw
+    double2* A = red_P2;  // pw x m, leading dimension pw
     if (hs_launch_ctrans(L + (size_t)r0 + (size_t)i0 * n, n, m, pw, A, pw, st) != cudaSuccess)
       return HS_ECUDA;
-    rc = split_gemm_ahb(A, pw, m, W + i0, n, ncols, pw, red_Z, st);
+    rc = split_gemm_ahb(A, pw, m, W + i0, n, ncols, pw, red_Z2, red_M2, st);
     if (rc) return rc;
-    if (hs_launch_sub(W + r0, n, red_Z, m, m, ncols, 0, fail, st) != cudaSuccess)
+    if (hs_launch_sub(W + r0, n, red_Z2, m, m, ncols, 0, fail, st) != cudaSuccess)
       return HS_ECUDA;
   }
   return HS_OK;

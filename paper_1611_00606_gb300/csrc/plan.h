@@ -102,13 +102,18 @@ struct hs_plan_s {
   double2 *red_W = nullptr, *red_P = nullptr;
   int red_cap = 0;
   int* red_fail = nullptr;
-  cudaEvent_t red_ev[5] = {};
+  cudaEvent_t red_ev[7] = {};
   // hs_reduce, split plans: slices of M = [L^{-H} | 0 | H] and of Z = H L^{-H} / 2,
   // 2 Z in FP64 (n x (n_pad + n)), the row weight 1/2; sized for red_split_cap
   SliceBuf red_M, red_Zs;
   double2* red_Z = nullptr;
   double* red_half = nullptr;
   int red_split_cap = 0;
+  // the inverse's own scratch (it runs on s_stream beside the Cholesky): slices,
+  // transposed L block, product; one event per Cholesky panel (its L columns final)
+  SliceBuf red_M2;
+  double2 *red_P2 = nullptr, *red_Z2 = nullptr;
+  std::vector<cudaEvent_t> red_pev;
 
   ServeState* serve = nullptr;
 
@@ -158,13 +163,16 @@ struct hs_plan_s {
   int split_reduce_alloc(int n);
   void split_reduce_release();
   // the Cholesky and the inverse of hs_reduce on split plans: FP64 panels of kRedPanel
-  // columns (rows), trailing updates as slice contractions (red_M, red_Z, red_P as scratch)
+  // columns (rows), trailing updates as slice contractions.  The Cholesky (scratch
+  // red_M, red_P, red_Z) records red_pev[p] once panel p is factored; the inverse
+  // (scratch red_M2, red_P2, red_Z2), on another stream, waits for it before block row p.
   int split_cholesky(double2* S, int n, int* fail, cudaStream_t st);
   int split_inverse(const double2* L, double2* W, int n, const int* fail, cudaStream_t st);
-  // lower(X^H X) and A^H B for K-major operands on the slice path (scratch: red_M)
-  int split_herk_lower(const double2* X, int ldX, int K, int nc, double2* out, cudaStream_t st);
+  // lower(X^H X) and A^H B for K-major operands on the slice path (slices in sb)
+  int split_herk_lower(const double2* X, int ldX, int K, int nc, double2* out, SliceBuf& sb,
+                       cudaStream_t st);
   int split_gemm_ahb(const double2* A, int ldA, int m, const double2* B, int ldB, int nc, int K,
-                     double2* out, cudaStream_t st);
+                     double2* out, SliceBuf& sb, cudaStream_t st);
   int check_device_error();
   void fill_info(hs_info* info, bool factored);
   bool serve_busy();
