@@ -218,7 +218,7 @@ int hs_assemble_static(const hs_z* A, const hs_z* B, const hs_z* T_AA, const hs_
  * contractions on the tensor cores with the plan's slice count; relative error about
  * 1e-10 kappa(S) instead of FP64's.  Complex plans
  * only (real plans: HS_EINVAL).  0 <= N_G <= N_G_max.  The plan allocates 32 N_G^2
- * bytes of device workspace on first use (split plans also about (24 s + 32) N_G^2
+ * bytes of device workspace on first use (split plans also about (24 s + 64) N_G^2
  * bytes of slices and products), grown on demand and
  * freed by hs_destroy; HS_ENOMEM if that fails.  Runs on the plan's stream and
  * returns when done.
