@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(kThreads) k_potrf_diag(double2* __restrict__ S
     a[e] = (r < jb && c < jb && r >= c) ? S[(size_t)(j0 + r) + (size_t)(j0 + c) * ld]
                                         : make_double2(0.0, 0.0);
   }
+  __shared__ double s_rl;  // 1 / L_kk of the current column
   for (int k = 0; k < jb; ++k) {
     __syncthreads();
     const double d = a[k * NB + k].x;
@@ -70,14 +71,21 @@ __global__ void __launch_bounds__(kThreads) k_potrf_diag(double2* __restrict__ S
       if (tid == 0) atomicCAS(fail, 0, j0 + k + 1);
       return;
     }
-    const double l = sqrt(d);
-    const double rl = 1.0 / l;
+    // one thread takes the square root and the reciprocal (FP64 issues slowly on this
+    // GPU: every warp repeating them cost as much as the column's update)
+    double l = 0.0;
+    if (tid == 0) {
+      l = sqrt(d);
+      s_rl = 1.0 / l;
+    }
+    __syncthreads();  // every thread has read d: the diagonal may now hold L_kk
+    if (tid == 0) a[k * NB + k] = make_double2(l, 0.0);
+    const double rl = s_rl;
     for (int r = k + 1 + tid; r < jb; r += kThreads) {
       a[k * NB + r].x *= rl;
       a[k * NB + r].y *= rl;
     }
     __syncthreads();
-    if (tid == 0) a[k * NB + k] = make_double2(l, 0.0);
     // trailing lower triangle: 16 x 16 threads over (row, column) pairs
     const int tx = tid & 15, ty = tid >> 4;
     for (int c = k + 1 + ty; c < jb; c += 16) {
