@@ -326,3 +326,17 @@ def test_reduce_not_positive_definite_reports_column():
     S = np.eye(3, dtype=np.complex128)
     S[1, 1] = np.nan
     assert reduce_standard(np.eye(3), S)[2] == 2
+
+
+def test_reduce_real_symmetric_pair_stays_real():
+    # Sec. 1.1: with inversion symmetry H and S are real symmetric; then L and C are
+    # real (zero imaginary parts exactly) and equal the real-arithmetic reduction
+    H, S = synth.reduce_inputs(30, seed=8, cond=1e2)
+    Hr, Sr = H.real.copy(), (S.real + S.real.T) / 2 + 30 * np.eye(30)
+    L, C, fail = reduce_standard(Hr.astype(np.complex128), Sr.astype(np.complex128))
+    assert fail == 0
+    assert np.all(L.imag == 0) and np.all(C.imag == 0)
+    Lx = np.linalg.cholesky(Sr)
+    Cx = np.linalg.solve(Lx, np.linalg.solve(Lx, Hr).T).T
+    assert np.allclose(L.real, Lx, rtol=0, atol=1e-13)
+    assert np.allclose(C.real, Cx, rtol=0, atol=1e-12)
