@@ -235,6 +235,12 @@ typedef struct {
   double ms_g;           /* G = P W^H and C = G + G^H */
 } hs_reduce_info;
 int hs_reduce(hs_plan_t plan, hs_z* H, hs_z* S, int N_G, hs_reduce_info* info);
+/* The same for the real-symmetric variant: real symmetric H and S (DEVICE pointers,
+ * N_G x N_G column-major, leading dimension N_G) on a plan made with HS_FP64 | HS_REAL;
+ * S <- L (real), H <- C (real symmetric).  The pair is embedded as complex and reduced
+ * by the FP64 kernels (imaginary parts stay exactly zero).  Split real plans:
+ * HS_ENOTSUP; complex plans: HS_EINVAL.  HS_ENOTPD leaves H and S unchanged. */
+int hs_reduce_real(hs_plan_t plan, double* H, double* S, int N_G, hs_reduce_info* info);
 
 /* Static description of an error code. */
 const char* hs_strerror(int code);

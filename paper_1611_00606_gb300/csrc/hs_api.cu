@@ -579,12 +579,8 @@ extern "C" int hs_destroy(hs_plan_t p) {
 // ---------------------------------------------------------------------------
 // Generalized-eigenproblem reduction (Sec. 1.1): S <- L, H <- L^{-1} H L^{-H}.
 
-extern "C" int hs_reduce(hs_plan_t p, hs_z* H, hs_z* S, int N_G, hs_reduce_info* info) {
-  if (info) std::memset(info, 0, sizeof(*info));
-  if (!p || !H || !S || N_G < 0 || N_G > p->N_G_max || p->real) return HS_EINVAL;
-  if (N_G == 0) return HS_OK;
-  if (H == S) return HS_EINVAL;
-  std::lock_guard<std::mutex> lk(p->mu);
+// The reduction of complex device buffers dH, dS (arguments checked, plan locked).
+static int reduce_locked(hs_plan_s* p, double2* dH, double2* dS, int N_G, hs_reduce_info* info) {
   if (p->red_cap < N_G) {
     free_ptr((void*&)p->red_W);
     free_ptr((void*&)p->red_P);
@@ -613,8 +609,6 @@ extern "C" int hs_reduce(hs_plan_t p, hs_z* H, hs_z* S, int N_G, hs_reduce_info*
     if (rc) return rc;
   }
   cudaStream_t st = p->stream;
-  double2* dH = (double2*)H;
-  double2* dS = (double2*)S;
   int fail = 0;
   HS_CUDA_TRY(cudaMemsetAsync(p->red_fail, 0, sizeof(int), st));
   HS_CUDA_TRY(cudaEventRecord(p->red_ev[0], st));
@@ -682,4 +676,35 @@ extern "C" int hs_reduce(hs_plan_t p, hs_z* H, hs_z* S, int N_G, hs_reduce_info*
     info->ms_total = el(0, 4);
   }
   return fail ? HS_ENOTPD : HS_OK;
+}
+
+extern "C" int hs_reduce(hs_plan_t p, hs_z* H, hs_z* S, int N_G, hs_reduce_info* info) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!p || !H || !S || N_G < 0 || N_G > p->N_G_max || p->real) return HS_EINVAL;
+  if (N_G == 0) return HS_OK;
+  if (H == S) return HS_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  return reduce_locked(p, (double2*)H, (double2*)S, N_G, info);
+}
+
+// Real symmetric pairs (Sec. 1.1): embedded as complex in the FP64 real plan's complex
+// H, S buffers, reduced by the complex FP64 kernels (imaginary parts stay exactly zero),
+// real parts copied back.
+extern "C" int hs_reduce_real(hs_plan_t p, double* H, double* S, int N_G, hs_reduce_info* info) {
+  if (info) std::memset(info, 0, sizeof(*info));
+  if (!p || !H || !S || N_G < 0 || N_G > p->N_G_max || !p->real) return HS_EINVAL;
+  if (p->precision != HS_FP64) return HS_ENOTSUP;
+  if (N_G == 0) return HS_OK;
+  if (H == S) return HS_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  if (!p->Hc || !p->Sc) return HS_ENOTSUP;
+  cudaStream_t st = p->stream;
+  HS_CUDA_TRY(hs_launch_embed2d(H, N_G, p->Hc, N_G, N_G, N_G, st));
+  HS_CUDA_TRY(hs_launch_embed2d(S, N_G, p->Sc, N_G, N_G, N_G, st));
+  const int rc = reduce_locked(p, p->Hc, p->Sc, N_G, info);
+  if (rc) return rc;  // HS_ENOTPD included: H and S are left unchanged
+  HS_CUDA_TRY(hs_launch_real_part(p->Hc, N_G, H, N_G, N_G, st));
+  HS_CUDA_TRY(hs_launch_real_part(p->Sc, N_G, S, N_G, N_G, st));
+  HS_CUDA_TRY(cudaStreamSynchronize(st));
+  return HS_OK;
 }

@@ -73,6 +73,7 @@ SIGNATURES = {
     "hs_assemble_real": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _VP, _VP,
                               C.POINTER(hs_info)]),
     "hs_reduce": (_I, [_VP, _VP, _VP, _I, C.POINTER(hs_reduce_info)]),
+    "hs_reduce_real": (_I, [_VP, _VP, _VP, _I, C.POINTER(hs_reduce_info)]),
 }
 
 
@@ -332,6 +333,22 @@ def hs_reduce(plan: int, H, S, N_G: int = None) -> dict:
     rc = _lib.hs_reduce(plan, _ptr(H), _ptr(S), N_G, C.byref(info))
     if rc < 0:
         err = HSError(rc, "hs_reduce")
+        err.fail_col = info.fail_col
+        raise err
+    return info.as_dict()
+
+
+def hs_reduce_real(plan: int, H, S, N_G: int = None) -> dict:
+    """Real-symmetric form of hs_reduce (plan made with "fp64_real"): float64 (N_G, N_G)
+    column-major CUDA tensors, reduced in place.  Returns the info dict; raises HSError
+    (HS_ENOTPD with ``fail_col``) when S is not positive definite."""
+    N_G = H.shape[0] if N_G is None else N_G
+    _check_real(H, (N_G, N_G), (1, N_G), "H")
+    _check_real(S, (N_G, N_G), (1, N_G), "S")
+    info = hs_reduce_info()
+    rc = _lib.hs_reduce_real(plan, _ptr(H), _ptr(S), N_G, C.byref(info))
+    if rc < 0:
+        err = HSError(rc, "hs_reduce_real")
         err.fail_col = info.fail_col
         raise err
     return info.as_dict()

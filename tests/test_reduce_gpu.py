@@ -211,3 +211,35 @@ def test_reduce_misuse(hs):
             hs.hs_reduce(p.h, Hd, Sd, 20)
         assert e.value.code == hs.HS_EINVAL
     assert np.array_equal(Hd.cpu().numpy(), H) and np.array_equal(Sd.cpu().numpy(), S)
+
+
+def test_reduce_real_fp64(hs):
+    """hs_reduce_real (real symmetric pairs, Sec. 1.1) on an FP64 real plan."""
+    n = 200
+    H, S = synth.reduce_inputs(n, seed=21, cond=1e3)
+    Hr, Sr = np.asfortranarray(H.real), np.asfortranarray(S.real)  # S.real is SPD
+    Hd, Sd = hs.to_device_real(Hr), hs.to_device_real(Sr)
+    with hs.Plan(1, 1, n, "fp64_real") as p:
+        info = hs.hs_reduce_real(p.h, Hd, Sd)
+    C, L = Hd.cpu().numpy(), Sd.cpu().numpy()
+    Lr, Cr, fail = reduce_standard(Hr, Sr)
+    assert fail == 0 and info["fail_col"] == 0
+    tol = _tol(Sr)
+    assert np.all(np.triu(L, 1) == 0)
+    assert rel_frobenius(L, Lr.real) <= tol and rel_frobenius(C, Cr.real) <= tol
+    assert np.array_equal(C, C.T)
+    # a failing pivot leaves both matrices unchanged
+    Sbad = Sr.copy()
+    Sbad[40, 40] = -1.0
+    Hd, Sd = hs.to_device_real(Hr), hs.to_device_real(Sbad)
+    with hs.Plan(1, 1, n, "fp64_real") as p:
+        with pytest.raises(hs.HSError) as e:
+            hs.hs_reduce_real(p.h, Hd, Sd)
+    assert e.value.code == hs.HS_ENOTPD and e.value.fail_col == reduce_standard(Hr, Sbad)[2]
+    assert np.array_equal(Hd.cpu().numpy(), Hr) and np.array_equal(Sd.cpu().numpy(), Sbad)
+    # split real plans are not supported, complex plans take hs_reduce
+    for prec, code in (("split_bf16_real", hs.HS_ENOTSUP), ("fp64", hs.HS_EINVAL)):
+        with hs.Plan(1, 1, n, prec) as p:
+            with pytest.raises(hs.HSError) as e:
+                hs.hs_reduce_real(p.h, Hd, Sd)
+            assert e.value.code == code
