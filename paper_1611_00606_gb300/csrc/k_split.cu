@@ -121,28 +121,6 @@ __device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* m
       "l"((uint64_t)map), "r"(0), "r"(0), "r"(kb), "r"(rb), "r"(plane), "r"(smem_u32(bar))
       : "memory");
 }
-// The same box, written at this smem offset into every CTA of the cluster in
-// `mask`, each CTA's mbarrier at `bar`'s offset receiving the byte count.
-__device__ __forceinline__ void tma_load_tile_mc(uint32_t dst, const CUtensorMap* map, int kb,
-                                                 int rb, int plane, uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      ".multicast::cluster [%0], [%1, {%2, %3, %4, %5, %6}], [%7], %8;" ::"r"(dst),
-      "l"((uint64_t)map), "r"(0), "r"(0), "r"(kb), "r"(rb), "r"(plane), "r"(smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// Every thread of every CTA of the cluster.
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile(
-      "barrier.cluster.arrive.release.aligned;\n\t"
-      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
 }
@@ -156,15 +134,6 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
-      : "memory");
-}
-// Arrive on the mbarrier at `bar`'s offset in every CTA of `mask` once this
-// thread's MMAs issued so far have completed.
-__device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(smem_u32(bar)),
-      "h"(mask)
       : "memory");
 }
 __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
@@ -413,12 +382,13 @@ __device__ __forceinline__ TileId decode_tile(const SplitParams& P, int tile) {
   TileId t{};
   constexpr bool R = is_real(MODE);  // column pairs of 2 x 128 real columns, pair c from row 2c
   if (is_contract(MODE)) {
-    // Clusters of two CTAs: column blocks 2c and 2c + 1 of one row block (which
-    // share the L' tiles); row block bi holds column pairs c <= bi (c < npr), so
-    // only an odd nbj leaves the last pair a block past the matrix (zero slices,
-    // nothing stored).  Pairs are numbered band by band (P.band row blocks per
-    // band) and column-major inside a band, so the CTAs resident at one time
-    // cover a compact block of rows x columns and share their operand tiles in L2.
+    // Consecutive tiles 2p, 2p + 1 are column blocks 2c and 2c + 1 of one row block
+    // (they read the same L' boxes, which the second finds in L2); row block bi
+    // holds column pairs c <= bi (c < npr), so only an odd nbj leaves the last pair
+    // a block past the matrix (zero slices, nothing stored).  Pairs are numbered
+    // band by band (P.band row blocks per band) and column-major inside a band, so
+    // the CTAs resident at one time cover a compact block of rows x columns and
+    // share their operand tiles in L2.
     const int npr = (P.nbj + 1) >> 1;
     int p = tile >> 1, bi = 0, c = 0;
     for (int b0 = P.bi0; b0 < P.nbi; b0 += P.band) {
@@ -439,7 +409,7 @@ __device__ __forceinline__ TileId decode_tile(const SplitParams& P, int tile) {
       p -= n;
     }
     t.i0 = bi * BM;
-    t.j0 = (2 * c + (int)cluster_rank()) * (R ? BN : BNC);
+    t.j0 = (2 * c + (tile & 1)) * (R ? BN : BNC);
     t.nseg = P.nseg;
     t.N_G = P.N_G;
   } else {
@@ -546,9 +516,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int s = S;
-  // CTAs per cluster: a contraction pairs two tiles of one row block, each CTA
-  // loading half of the shared L' boxes for both (TMA multicast)
-  constexpr int CL = is_contract(MODE) ? 2 : 1;
   const int NS = P.n_stage;
   const uint32_t a_bytes = (uint32_t)s * 2 * TILE_BYTES;   // s slices x 128 rows
   const uint32_t stage_bytes = 2 * a_bytes;                 // A part + B part
@@ -567,7 +534,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   if (threadIdx.x == 0) {
     for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], CL);  // released by the MMA thread of every CTA
+      mbar_init(&empty[i], 1);  // released by the MMA thread's commit
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, NUM_DRAIN_WARPS);
@@ -591,21 +558,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   }
   tc_fence_before();
   __syncthreads();
-  if (CL > 1) cluster_sync();  // the peer's barriers are initialised before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
     // ---------------- TMA producer: lane 0 waits for free stages and arms them;
     // the stage's boxes are then issued by one lane each, in one warp instruction
-    constexpr int NB = CL == 1 ? 4 : 3;  // boxes per slice: L' (two halves or ours), R', R''
+    constexpr int NB = 4;  // boxes per slice: the two 64-row halves of L', R', R''
     int slot = 0;
     uint32_t phase = 0;
     uint32_t armed = 0;        // bit i: slot i was armed at least once
     uint32_t armed_par = 0;    // bit i: parity of the last armed phase of slot i
     bool ok = true;
     const int bp = lane / NB, bk = lane - bp * NB;  // this lane's slice and box kind
-    const int h = (int)cluster_rank();
     for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
      const TileId T = decode_tile<MODE>(P, tile);
      for (int sg = 0; sg < T.nseg && ok; ++sg) {
@@ -624,19 +589,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
         const int kl = si.kbL + kb, kr = si.kbR + kb;
         if (bp < s) {
           const uint32_t da = sa + bp * 2 * TILE_BYTES, db = sb + bp * 2 * TILE_BYTES;
-          if (CL == 1) {
-            if (bk == 0) tma_load_tile(da, si.mL, kl, si.rbL, si.plL + bp, &full[slot]);
-            else if (bk == 1)
-              tma_load_tile(da + TILE_BYTES, si.mL, kl, si.rbL + 1, si.plL + bp, &full[slot]);
-            else if (bk == 2) tma_load_tile(db, si.mR1, kr, si.rbR1, si.plR + bp, &full[slot]);
-            else tma_load_tile(db + TILE_BYTES, si.mR2, kr, si.rbR2, si.plR + bp, &full[slot]);
-          } else {  // bk 0: this CTA's 64-row half of the L' box, into both CTAs
-            if (bk == 0)
-              tma_load_tile_mc(da + h * TILE_BYTES, si.mL, kl, si.rbL + h, si.plL + bp, &full[slot],
-                               (uint16_t)0x3);
-            else if (bk == 1) tma_load_tile(db, si.mR1, kr, si.rbR1, si.plR + bp, &full[slot]);
-            else tma_load_tile(db + TILE_BYTES, si.mR2, kr, si.rbR2, si.plR + bp, &full[slot]);
-          }
+          if (bk == 0) tma_load_tile(da, si.mL, kl, si.rbL, si.plL + bp, &full[slot]);
+          else if (bk == 1)
+            tma_load_tile(da + TILE_BYTES, si.mL, kl, si.rbL + 1, si.plL + bp, &full[slot]);
+          else if (bk == 2) tma_load_tile(db, si.mR1, kr, si.rbR1, si.plR + bp, &full[slot]);
+          else tma_load_tile(db + TILE_BYTES, si.mR2, kr, si.rbR2, si.plR + bp, &full[slot]);
         }
         __syncwarp();
         if (++slot == NS) {
@@ -658,14 +615,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           while (!mbar_try(&full[i], (armed_par >> i) & 1u))
             if (globaltimer() - t0 > kWaitNs) break;
         }
-      // nor with the peer's releases of this CTA's stages still to arrive
-      if (CL > 1 && ok && !*abort_flag)
-        for (int i = 0; i < NS; ++i)
-          if (armed & (1u << i)) {
-            uint64_t t0 = globaltimer();
-            while (!mbar_try(&empty[i], (armed_par >> i) & 1u))
-              if (globaltimer() - t0 > kWaitNs) break;
-          }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer (one thread)
@@ -697,8 +646,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
             const uint32_t sa = smem_u32(smem + slot * stage_bytes);
             issue_stage<S>(tmem, sdesc_sw32(sa), sdesc_sw32(sa + a_bytes),
                            kb == w0 ? first_mask : 0u);
-            if (CL == 1) tc_commit(&empty[slot]);
-            else tc_commit_mc(&empty[slot], (uint16_t)0x3);
+            tc_commit(&empty[slot]);
             if (++slot == NS) {
               slot = 0;
               phase ^= 1u;
@@ -880,7 +828,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
 
   tc_fence_before();
   __syncthreads();
-  if (CL > 1) cluster_sync();  // no multicast or remote arrive targets an exited CTA
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
@@ -1363,25 +1310,8 @@ template <int MODE, int S>
 static int launch_one(int grid, size_t smem, cudaStream_t st, const SplitParams& P) {
   int rc = set_smem((const void*)k_split_gemm<MODE, S>, smem);
   if (rc) return rc;
-  if (!is_contract(MODE)) {
-    k_split_gemm<MODE, S><<<grid, NUM_THREADS, smem, st>>>(P);
-    return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
-  }
-  // contraction: clusters of two CTAs (grid is even)
-  if (grid % 2 != 0) return HS_EINVAL;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(NUM_THREADS);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_split_gemm<MODE, S>, P) == cudaSuccess ? HS_OK : HS_ECUDA;
+  k_split_gemm<MODE, S><<<grid, NUM_THREADS, smem, st>>>(P);
+  return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
 }
 
 template <int MODE>
@@ -1551,7 +1481,7 @@ int tuned_depth(int mode, int s, int N_L, int N_G, int max_depth, bool allow, cu
 }
 }  // namespace
 
-// Row blocks per band of the contraction's tile order: 8 (76 resident clusters
+// Row blocks per band of the contraction's tile order: 8 (152 resident CTAs
 // then span about 8 row blocks x 19 column blocks); HS_BAND overrides.
 static int contract_band() {
   static const int band = []() {

@@ -23,15 +23,15 @@ def rows_pad(n):
 
 def contraction_tiles(bi0, nbi, nbj, band=8):
     """(row origin, column origin) of every CTA of a lower-triangle contraction:
-    clusters of two column blocks of one row block, pairs c <= row block, row blocks
-    in bands, column-major inside a band."""
+    consecutive CTAs 2p, 2p + 1 take column blocks 2c, 2c + 1 of one row block, pairs
+    c <= row block, row blocks in bands, column-major inside a band."""
     npr = (nbj + 1) >> 1
     out = []
     for b0 in range(bi0, nbi, band):
         b1 = min(b0 + band, nbi)
         for c in range(npr):
             for bi in range(max(b0, c), b1):
-                out += [(bi * BM, (2 * c + rank) * BNC) for rank in (0, 1)]
+                out += [(bi * BM, (2 * c + half) * BNC) for half in (0, 1)]
     return out
 
 
