@@ -90,6 +90,46 @@ def test_haa_identity_equals_overlap_of_A():
     assert rel_frobenius(h_aa(d["A"], I, N_A, N_L), S) < 1e-14
 
 
+@pytest.mark.parametrize("N_A,N_L,N_G,indef", [(2, 4, 5, ()), (3, 4, 6, (1,))])
+def test_haa_general_hermitian_T_exact(N_A, N_L, N_G, indef):
+    """H_AA at a general Hermitian T^AA (complex off-diagonal entries) against the exact
+    index form with B = 0, where Eq. (h) reduces to its first under-brace.  A slip that
+    applies T^T (= conj(T) for Hermitian T) or conj(A) on the wrong side is caught."""
+    d = _inputs(N_A, N_L, N_G, indef, seed=13)
+    T = d["T_AA"]
+    assert np.abs(T - np.conj(np.swapaxes(T, -1, -2))).max() == 0      # Hermitian
+    assert np.abs(np.imag(T[:, 0, 1])).min() > 0                        # not real
+    Z = np.zeros_like(d["B"])
+    He, _ = brute.exact_hs(d["A"], Z, T, d["T_AB"], d["T_BB"], d["U"], N_A, N_L)
+    He = brute.to_complex(He)
+    Hb, _ = brute.abs_sum_bound(d["A"], Z, T, d["T_AB"], d["T_BB"], d["U"], N_A, N_L)
+    n = N_L * N_L + 4
+    H = h_aa(d["A"], T, N_A, N_L)
+    assert np.all(np.abs(H - He) <= n * EPS * Hb + 1e-300)
+    # the same H_AA is the whole H of Eq. (h) when B = 0
+    Hf, _ = assemble(d["A"], Z, T, d["T_AB"], d["T_BB"], d["U"], N_A, N_L)
+    assert rel_frobenius(Hf, He) < 1e-14
+    # negative controls: transposed T, conjugate on the right-hand factor
+    wrong_t = np.zeros_like(He)
+    wrong_c = np.zeros_like(He)
+    for a in range(N_A):
+        Aa = d["A"][a * N_L:(a + 1) * N_L]
+        wrong_t += Aa.conj().T @ T[a].T @ Aa
+        wrong_c += Aa.T @ T[a] @ Aa.conj()
+    assert rel_frobenius(wrong_t, He) > 1e-3
+    assert rel_frobenius(wrong_c, He) > 1e-3
+
+
+def test_haa_matches_assemble_with_zero_b_at_scale():
+    """B = 0 at a paper-like shape with indefinite atoms: h_aa equals the full
+    definition (both pinned by the exact index form at tiny sizes)."""
+    N_A, N_L, N_G = 5, 49, 300
+    d = _inputs(N_A, N_L, N_G, (1, 3), seed=14)
+    Z = np.zeros_like(d["B"])
+    Hf, _ = assemble(d["A"], Z, d["T_AA"], d["T_AB"], d["T_BB"], d["U"], N_A, N_L)
+    assert rel_frobenius(h_aa(d["A"], d["T_AA"], N_A, N_L), Hf) < 1e-14
+
+
 def test_hermitian():
     N_A, N_L, N_G = 4, 16, 256
     d = _inputs(N_A, N_L, N_G, (3,), seed=0)
