@@ -129,6 +129,27 @@ int hs_assemble_host(hs_plan_t plan, const hs_z* A, const hs_z* B,
                      const hs_z* T_AA, const hs_z* T_AB, const hs_z* T_BB, const double* U,
                      int N_A, int N_L, int N_G, hs_z* H, hs_z* S, hs_info* info);
 
+/* K-split over atoms (the paper's multi-GPU experiments, Sec. 4, split one k-point's
+ * work; here each rank of a process group takes one range of atoms).  Eqs. (h) and (s)
+ * are sums over atoms, so H = sum_r H_r and S = sum_r S_r over disjoint atom ranges r.
+ * hs_assemble_partial computes the terms of the plan's N_A atoms only: A and B point at
+ * the first row of the range inside the full stacked arrays (row a0 * N_L of a
+ * K_total x N_G array, ld_AB = K_total >= N_A * N_L), T_AA, T_AB, T_BB at the range's
+ * first N_L x N_L block, U at its first row (U + a0 * N_L).  It writes the LOWER
+ * triangles (diagonal included) of H_r and S_r; the strict upper triangles are left
+ * undefined (they may hold parts of the contraction's diagonal tiles or whatever the
+ * buffers held before).  The caller adds the partials of all ranges element by element
+ * (for example one collective sum over the ranks' H and S buffers), then calls
+ * hs_finalize on the sums, which fills the upper triangles as the conjugates of the
+ * lower ones and sets Im(diag) = 0: the result equals hs_assemble's up to the rounding
+ * of the additions.  Failing Cholesky factorisations are found and counted per range
+ * (hs_info.n_fallback counts this range's).  Pointers are DEVICE pointers; both calls
+ * block until done; complex plans only (real plans: HS_EINVAL). */
+int hs_assemble_partial(hs_plan_t plan, const hs_z* A, const hs_z* B, int ld_AB,
+                        const hs_z* T_AA, const hs_z* T_AB, const hs_z* T_BB, const double* U,
+                        int N_A, int N_L, int N_G, hs_z* H, hs_z* S, hs_info* info);
+int hs_finalize(hs_plan_t plan, hs_z* H, hs_z* S, int N_G);
+
 /* Serving: enqueue one k-point request (device pointers, layout above; A and B
  * may be column-truncated views of wider arrays: ld_AB >= K is their leading
  * dimension).  T and U must be the plan's current T (hs_set_t) and a U of the
@@ -172,16 +193,18 @@ int hs_assemble_real(hs_plan_t plan, const double* A, const double* B, const dou
 
 /* ---------------------------------------------------------------------------
  * Allocation-free FP64 assembly (a library addition; the paper has no
- * counterpart).  For callers that may not allocate device memory -- code
- * running under strict CUDA-graph capture, inside someone else's fixed memory
- * arena, or in a host that locks its device footprint after start-up.  It runs
- * the plain FP64 path of hs_assemble (same kernels, same results) without a
- * plan: all intermediate buffers live in one file-scope device array of
- * HS_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the
- * process exits.  Nothing is allocated and nothing is cached between calls.
+ * counterpart).  For callers that may not allocate device memory: code that runs
+ * inside someone else's fixed memory arena, or in a host process that locks its
+ * device footprint after start-up, cannot create a plan, because hs_plan allocates
+ * its workspace.  This call runs the plain FP64 path of hs_assemble (same kernels,
+ * same results) without a plan: all intermediate buffers live in one file-scope
+ * device array of HS_STATIC_SCRATCH_BYTES that every GPU loading the library holds
+ * until the process exits.  Nothing is allocated and nothing is cached between calls.
  *
  * Pointers are DEVICE pointers with the layout above; stream is a cudaStream_t
- * (NULL = legacy default stream).  Returns after H and S are complete.
+ * (NULL = legacy default stream).  The call synchronises that stream once midway
+ * (it reads the number of atoms whose Cholesky failed back to the host to size the
+ * fallback segment) and again at the end; it returns after H and S are complete.
  * Size limit: the call needs
  *   align256(16 N_A N_L^2) + align256(32 N_A N_L^2) + 3 align256(4 N_A) + 256
  *   + 3 align256(16 N_A N_L N_G)

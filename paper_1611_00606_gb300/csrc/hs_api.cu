@@ -128,6 +128,8 @@ void hs_plan_s::release() {
   split_reduce_release();
   for (auto& e : red_ev)
     if (e) { cudaEventDestroy(e); e = nullptr; }
+  for (auto& e : real_ev)
+    if (e) { cudaEventDestroy(e); e = nullptr; }
   for (auto& e : copy_ev)
     if (e) { cudaEventDestroy(e); e = nullptr; }
   if (copy_stream) { cudaStreamDestroy(copy_stream); copy_stream = nullptr; }
@@ -254,13 +256,13 @@ extern "C" int hs_set_t(hs_plan_t p, const hs_z* T_AA, const hs_z* T_AB, const h
 // must be current).  ev[3..8] bracket the phases for hs_info when timed.
 int hs_plan_s::enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G,
                        double2* H, double2* S, Workspace& w, cudaStream_t st, bool timed,
-                       cudaEvent_t s_done, bool presliced) {
+                       cudaEvent_t s_done, bool presliced, bool mirror) {
   const int K = N_A * N_L;
   const int N_h = N_A - N_f;
   if (w.N_G < N_G || w.n_fail < N_f) return HS_EINVAL;
   if (timed && !presliced) HS_CUDA_TRY(cudaEventRecord(ev[3], st));
   if (precision == HS_SPLIT_BF16) {
-    int rc = split_enqueue(A, B, ldAB, U, N_G, H, S, w, st, timed, s_done, presliced);
+    int rc = split_enqueue(A, B, ldAB, U, N_G, H, S, w, st, timed, s_done, presliced, mirror);
     if (rc != HS_OK) return rc;
   } else {
     HS_CUDA_TRY(hs_launch_atoms_fp64(MZ, M2, fail_d, slot_d, A, B, ldAB, w.Z, w.W2, K, N_A, N_L,
@@ -280,15 +282,19 @@ int hs_plan_s::enqueue(const double2* A, const double2* B, int ldAB, const doubl
     sH.n = n;
     if (timed) HS_CUDA_TRY(cudaEventRecord(ev[5], st));
     HS_CUDA_TRY(hs_launch_contract_fp64(sS, S, N_G, N_G, st));
-    HS_CUDA_TRY(hs_launch_mirror(S, N_G, N_G, st));  // S final: it can leave while H runs
+    if (mirror) HS_CUDA_TRY(hs_launch_mirror(S, N_G, N_G, st));  // S final: it can leave
     if (s_done) HS_CUDA_TRY(cudaEventRecord(s_done, st));
     if (timed) HS_CUDA_TRY(cudaEventRecord(ev[6], st));
     HS_CUDA_TRY(hs_launch_contract_fp64(sH, H, N_G, N_G, st));
     if (timed) HS_CUDA_TRY(cudaEventRecord(ev[7], st));
   }
   // (S was mirrored right after its contraction)
-  if (real && precision == HS_SPLIT_BF16) HS_CUDA_TRY(hs_launch_mirror_real((double*)H, N_G, N_G, st));
-  else HS_CUDA_TRY(hs_launch_mirror(H, N_G, N_G, st));
+  if (!mirror) {
+  } else if (real && precision == HS_SPLIT_BF16) {
+    HS_CUDA_TRY(hs_launch_mirror_real((double*)H, N_G, N_G, st));
+  } else {
+    HS_CUDA_TRY(hs_launch_mirror(H, N_G, N_G, st));
+  }
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[8], st));
   return HS_OK;
 }
@@ -374,6 +380,46 @@ extern "C" int hs_assemble(hs_plan_t p, const hs_z* A, const hs_z* B, const hs_z
   rc = p->check_device_error();
   if (rc) return rc;
   p->fill_info(info, factored);
+  return HS_OK;
+}
+
+// K-split over atoms (the multi-GPU form of Sec. 4, one atom range per rank): the terms
+// of this plan's atoms, lower triangles only; the caller sums the partials of all atom
+// ranges and calls hs_finalize.
+extern "C" int hs_assemble_partial(hs_plan_t p, const hs_z* A, const hs_z* B, int ld_AB,
+                                   const hs_z* T_AA, const hs_z* T_AB, const hs_z* T_BB,
+                                   const double* U, int N_A, int N_L, int N_G, hs_z* H,
+                                   hs_z* S, hs_info* info) {
+  int rc = check_args(p, A, B, T_AA, T_AB, T_BB, U, N_A, N_L, N_G, H, S);
+  if (rc) return rc;
+  if (p->real || ld_AB < N_A * N_L) return HS_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  bool factored = false;
+  if (!p->t_valid || p->tAA != (const void*)T_AA || p->tAB != (const void*)T_AB ||
+      p->tBB != (const void*)T_BB) {
+    if (p->serve_busy()) return HS_EBUSY;
+    rc = p->factor((const double2*)T_AA, (const double2*)T_AB, (const double2*)T_BB);
+    if (rc) return rc;
+    factored = true;
+  }
+  rc = ensure_sync_ws(p);
+  if (rc) return rc;
+  rc = p->enqueue((const double2*)A, (const double2*)B, ld_AB, U, N_G, (double2*)H, (double2*)S,
+                  p->ws, p->stream, true, nullptr, false, /*mirror=*/false);
+  if (rc) return rc;
+  HS_CUDA_TRY(cudaStreamSynchronize(p->stream));
+  rc = p->check_device_error();
+  if (rc) return rc;
+  p->fill_info(info, factored);
+  return HS_OK;
+}
+
+extern "C" int hs_finalize(hs_plan_t p, hs_z* H, hs_z* S, int N_G) {
+  if (!p || !H || !S || H == S || p->real || N_G < 1 || N_G > p->N_G_max) return HS_EINVAL;
+  std::lock_guard<std::mutex> lk(p->mu);
+  HS_CUDA_TRY(hs_launch_mirror((double2*)H, N_G, N_G, p->stream));
+  HS_CUDA_TRY(hs_launch_mirror((double2*)S, N_G, N_G, p->stream));
+  HS_CUDA_TRY(cudaStreamSynchronize(p->stream));
   return HS_OK;
 }
 
@@ -699,12 +745,23 @@ extern "C" int hs_reduce_real(hs_plan_t p, double* H, double* S, int N_G, hs_red
   std::lock_guard<std::mutex> lk(p->mu);
   if (!p->Hc || !p->Sc) return HS_ENOTSUP;
   cudaStream_t st = p->stream;
+  for (auto& e : p->real_ev)
+    if (!e) HS_CUDA_TRY(cudaEventCreate(&e));
+  HS_CUDA_TRY(cudaEventRecord(p->real_ev[0], st));
   HS_CUDA_TRY(hs_launch_embed2d(H, N_G, p->Hc, N_G, N_G, N_G, st));
   HS_CUDA_TRY(hs_launch_embed2d(S, N_G, p->Sc, N_G, N_G, N_G, st));
   const int rc = reduce_locked(p, p->Hc, p->Sc, N_G, info);
   if (rc) return rc;  // HS_ENOTPD included: H and S are left unchanged
   HS_CUDA_TRY(hs_launch_real_part(p->Hc, N_G, H, N_G, N_G, st));
   HS_CUDA_TRY(hs_launch_real_part(p->Sc, N_G, S, N_G, N_G, st));
+  HS_CUDA_TRY(cudaEventRecord(p->real_ev[1], st));
   HS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (info) {  // the whole call's device time: the embedding and the copies back included
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->real_ev[0], p->real_ev[1]) == cudaSuccess)
+      info->ms_total = ms;
+    else
+      cudaGetLastError();
+  }
   return HS_OK;
 }

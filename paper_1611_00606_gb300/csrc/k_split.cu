@@ -1619,7 +1619,7 @@ int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGr
 // 3. gather A_f, slice the per-atom outputs, and the two stacked contractions
 int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, double2* S,
                              Workspace& w, cudaStream_t st, bool timed, cudaEvent_t s_done,
-                             bool skip_S) {
+                             bool skip_S, bool mirror) {
   const int K = N_A * N_L;
   const int N_h = N_A - N_f;
   const int s = slices;
@@ -1717,7 +1717,7 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
     smem = smem_for(mode, depth, stage_bytes);
   }
   if (!skip_S) rc = launch_gemm(mode, s, tiles, smem, st, P);
-  if (rc == HS_OK && !skip_S) {  // S is final once mirrored: it can leave while H is computed
+  if (rc == HS_OK && !skip_S && mirror) {  // S is final once mirrored: it can leave while H runs
     const cudaError_t e = real ? hs_launch_mirror_real((double*)S, N_G, N_G, st)
                                : hs_launch_mirror(S, N_G, N_G, st);
     if (e != cudaSuccess || (s_done && cudaEventRecord(s_done, st) != cudaSuccess)) rc = HS_ECUDA;
@@ -1806,14 +1806,14 @@ int hs_plan_s::split_contract_S_rows(int N_G, double2* S, Workspace& w, cudaStre
 
 int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const double* U,
                              int N_G, double2* H, double2* S, Workspace& w, cudaStream_t st,
-                             bool timed, cudaEvent_t s_done, bool presliced) {
+                             bool timed, cudaEvent_t s_done, bool presliced, bool mirror) {
   int rc = presliced ? HS_OK : split_inputs(A, B, ldAB, U, N_G, w, st);
   if (rc) return rc;
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[9], st));
   AtomsJob job{&w, N_G};
   rc = split_atoms(&job, 1, st, nullptr);
   if (rc) return rc;
-  return split_outputs(A, ldAB, N_G, H, S, w, st, timed, s_done, presliced);
+  return split_outputs(A, ldAB, N_G, H, S, w, st, timed, s_done, presliced, mirror);
 }
 
 // ---------------------------------------------------------------------------

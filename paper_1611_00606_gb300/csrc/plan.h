@@ -103,6 +103,7 @@ struct hs_plan_s {
   int red_cap = 0;
   int* red_fail = nullptr;
   cudaEvent_t red_ev[7] = {};
+  cudaEvent_t real_ev[2] = {};  // hs_reduce_real: around its copies in and out
   // hs_reduce, split plans: slices of M = [L^{-H} | 0 | H] and of Z = H L^{-H} / 2,
   // 2 Z in FP64 (n x (n_pad + n)), the row weight 1/2; sized for red_split_cap
   SliceBuf red_M, red_Zs;
@@ -135,13 +136,15 @@ struct hs_plan_s {
   size_t ws_elem() const { return real && precision == HS_SPLIT_BF16 ? 8 : 16; }
   // s_done (optional): recorded on st once S (mirrored) is final, while H is still being
   // computed; presliced (split form): the caller already sliced the inputs and contracted
-  // and mirrored S (the host call's streamed path)
+  // and mirrored S (the host call's streamed path); mirror = false: the lower triangles of
+  // H and S only, the upper triangles left as the contraction leaves them (partial sums
+  // over an atom range, mirrored after they are added up)
   int enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G, double2* H,
               double2* S, Workspace& w, cudaStream_t st, bool timed, cudaEvent_t s_done = nullptr,
-              bool presliced = false);
+              bool presliced = false, bool mirror = true);
   int split_enqueue(const double2* A, const double2* B, int ldAB, const double* U, int N_G,
                     double2* H, double2* S, Workspace& w, cudaStream_t st, bool timed,
-                    cudaEvent_t s_done = nullptr, bool presliced = false);
+                    cudaEvent_t s_done = nullptr, bool presliced = false, bool mirror = true);
   int split_geometry(int& n_stage, size_t& smem) const;
   // g0, ng: slice only operand columns [g0, g0 + ng) (ng < 0: every column and the zero
   // rows up to the padded row count)
@@ -152,7 +155,7 @@ struct hs_plan_s {
   // skip_S: S was already contracted and mirrored by the caller
   int split_outputs(const double2* A, int ldAB, int N_G, double2* H, double2* S, Workspace& w,
                     cudaStream_t st, bool timed, cudaEvent_t s_done = nullptr,
-                    bool skip_S = false);
+                    bool skip_S = false, bool mirror = true);
   // S contraction tiles of row blocks [bi0, bi1) only (no mirror)
   int split_contract_S_rows(int N_G, double2* S, Workspace& w, cudaStream_t st, int bi0,
                             int bi1);

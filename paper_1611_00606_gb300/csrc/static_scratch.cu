@@ -1,15 +1,14 @@
 // hs_assemble_static: the FP64 assembly for small problems without any device
 // allocation.
 //
-// Some callers cannot call cudaMalloc at all: code that runs while a CUDA
-// graph is being captured with a strict capture mode, code inside a memory
-// pool or arena owned by someone else that forbids side allocations, or hosts
-// whose allocator is locked down (for example an embedding that has to keep
-// its device footprint fixed after start-up).  hs_plan() allocates its
-// workspace, so those callers cannot use it.  This entry point instead keeps
-// the whole per-call workspace (per-atom operators, Cholesky flags, Z, [Y; X],
-// the stacked A rows of failing atoms) in one statically sized device array
-// that the CUDA runtime reserves when the library is loaded.
+// Some callers cannot call cudaMalloc at all: code inside a memory pool or arena
+// owned by someone else that forbids side allocations, or hosts whose allocator is
+// locked down (for example an embedding that has to keep its device footprint fixed
+// after start-up).  hs_plan() allocates its workspace, so those callers cannot use
+// it.  This entry point instead keeps the whole per-call workspace (per-atom
+// operators, Cholesky flags, Z, [Y; X], the stacked A rows of failing atoms) in one
+// statically sized device array that the CUDA runtime reserves when the library is
+// loaded.
 //
 // The array is a file-scope __device__ symbol: in host code its name is only
 // a host-side stand-in, not a device address, so the first call on each device

@@ -64,6 +64,9 @@ SIGNATURES = {
     "hs_assemble_host": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _VP, _VP,
                               C.POINTER(hs_info)]),
     "hs_submit": (_I, [_VP, _VP, _VP, _I, _VP, _I, _VP, _VP, C.POINTER(_I64)]),
+    "hs_assemble_partial": (_I, [_VP, _VP, _VP, _I, _VP, _VP, _VP, _VP, _I, _I, _I, _VP, _VP,
+                                 C.POINTER(hs_info)]),
+    "hs_finalize": (_I, [_VP, _VP, _VP, _I]),
     "hs_poll": (_I, [_VP, _I64, _I64, C.POINTER(hs_info)]),
     "hs_fallback_flags": (_I, [_VP, C.POINTER(_I)]),
     "hs_destroy": (_I, [_VP]),
@@ -213,6 +216,34 @@ def hs_assemble_host(plan: int, A, B, T_AA, T_AB, T_BB, U, N_A: int, N_L: int, N
                                  _ptr(U), N_A, N_L, N_G, _ptr(H), _ptr(S), C.byref(info)),
            "hs_assemble_host")
     return info.as_dict()
+
+
+def hs_assemble_partial(plan: int, A, B, T_AA, T_AB, T_BB, U, N_A: int, N_L: int, N_G: int,
+                        H, S) -> dict:
+    """Terms of one atom range (the plan's N_A atoms), lower triangles of H and S only.
+    A, B: row views (N_A*N_L, >= N_G) of the full stacked arrays (leading dimension
+    >= N_A*N_L); T_*: (N_A, N_L, N_L) views of the range's blocks; U: (N_A, N_L)."""
+    K = N_A * N_L
+    ld = _check_coef(A, K, N_G, "A")
+    if _check_coef(B, K, N_G, "B") != ld:
+        raise ValueError("hs_assemble_partial: A and B must share a leading dimension")
+    for T, n in ((T_AA, "T_AA"), (T_AB, "T_AB"), (T_BB, "T_BB")):
+        _check_T(T, N_A, N_L, n)
+    _check_out(H, N_G, "H")
+    _check_out(S, N_G, "S")
+    info = hs_info()
+    _check(_lib.hs_assemble_partial(plan, _ptr(A), _ptr(B), ld, _ptr(T_AA), _ptr(T_AB),
+                                    _ptr(T_BB), _ptr(U), N_A, N_L, N_G, _ptr(H), _ptr(S),
+                                    C.byref(info)), "hs_assemble_partial")
+    return info.as_dict()
+
+
+def hs_finalize(plan: int, H, S, N_G: int) -> None:
+    """Upper triangles := conjugates of the lower ones, Im(diag) := 0 (after the partial
+    sums of all atom ranges were added up)."""
+    _check_out(H, N_G, "H")
+    _check_out(S, N_G, "S")
+    _check(_lib.hs_finalize(plan, _ptr(H), _ptr(S), N_G), "hs_finalize")
 
 
 def hs_submit(plan: int, A, B, U, N_G: int, H, S) -> int:

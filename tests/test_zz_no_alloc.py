@@ -1,8 +1,9 @@
 """hs_assemble_static: the allocation-free FP64 assembly.
 
-Callers that may not allocate device memory (strict graph capture, fixed
-arenas, locked device footprints) use this entry point; its intermediates
-live in the library's static device scratch instead of a plan's workspace.
+Callers that may not allocate device memory (code inside someone else's fixed
+memory arena, or a host process that locks its device footprint after start-up)
+use this entry point; its intermediates live in the library's static device
+scratch instead of a plan's workspace.
 Its H and S must match hs_assemble (FP64 plan) within the FP64 parity
 tolerance, on two calls in a row (the scratch keeps the previous call's
 contents, which must not leak into the next result).  This file is named to
@@ -64,3 +65,19 @@ def test_static_entry_rejects_problems_above_its_scratch(hs):
                                     A.data_ptr() + 16, A.data_ptr() + 32, None)
     assert rc == hs.HS_ESCRATCH
     assert 3 * 16 * K * N_G > 32 * 2 ** 20  # HS_STATIC_SCRATCH_BYTES in include/hs.h
+
+
+def test_static_entry_allocates_no_device_memory(hs):
+    """After a first call (which looks up the scratch address and loads the kernels),
+    further calls leave the device's free memory unchanged: nothing is allocated."""
+    w = synth.Workload("m", 3, 16, 200, (1,), seed=23)
+    args = _device_inputs(hs, w)
+    H, S = hs.empty_hs(w.N_G), hs.empty_hs(w.N_G)
+    hs.hs_assemble_static(*args, w.N_A, w.N_L, w.N_G, H, S)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        hs.hs_assemble_static(*args, w.N_A, w.N_L, w.N_G, H, S)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
