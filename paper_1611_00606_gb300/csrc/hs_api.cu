@@ -99,8 +99,8 @@ void hs_plan_s::ws_free(Workspace& w, cudaStream_t st) {
   free_ws_ptr((void*&)w.AF, w.async, st);
   for (auto& b : w.sb) {
     free_ws_ptr((void*&)b.plain, w.async, st);
-    free_ws_ptr((void*&)b.rot, w.async, st);
     free_ws_ptr((void*&)b.expo, w.async, st);
+    b.rot = false;
   }
   w.N_G = 0;
   w.n_fail = 0;

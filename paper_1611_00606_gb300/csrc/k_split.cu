@@ -111,8 +111,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
     }
   }
 }
-// One 64-row x 16-element box of a blocked slice array (coordinates: k block,
-// 64-row block, plane = slice [+ atom]); the box is contiguous in global memory.
+// One box of a blocked slice array starting at (k block, 64-row block, plane); the
+// tensor map's box holds 16 elements x 64 rows x 1 k block x (1 or 2) row blocks x
+// (s or 2 s) planes, laid out in shared memory in that order, 2 KB per (row block,
+// plane): one instruction brings in a whole operand of a pipeline stage.
 __device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* map, int kb, int rb,
                                               int plane, uint64_t* bar) {
   asm volatile(
@@ -310,7 +312,8 @@ __host__ __device__ constexpr bool is_contract(int mode) { return (mode & 1) == 
 __host__ __device__ constexpr bool is_real(int mode) { return mode >= 2; }
 
 struct SplitSeg {
-  int mL, mR, mRr;  // tensor maps of L', R', R''
+  int mL, mR;       // tensor maps: L' as the left operand, R as the right one
+                    // (complex: its plain and rotated slices, interleaved by plane)
   int kblocks;      // stages of KB real K
   const int* eL;    // exponents of the L source columns
   const int* eR;    // exponents of the R source columns
@@ -352,6 +355,8 @@ struct SplitParams {
   int rows_pad;   // slice p of a coefficient-side array starts at row p * rows_pad
   double2* C;
   int* err;
+  int stall;  // test only: the producer arms no stage and issues no copy, so the MMA
+              // thread's and the drain's waits run out (failure-path test)
   AtomsArgs at;
 };
 
@@ -359,10 +364,9 @@ struct SplitParams {
 // plane = slice p (+ atom * s for operators), 64-row blocks, 16-wide K blocks).
 struct SegInfo {
   const CUtensorMap* mL;
-  const CUtensorMap* mR1;
-  const CUtensorMap* mR2;
+  const CUtensorMap* mR;
   int kbL, rbL, plL;        // L side: first K block, first 64-row block, plane of slice 0
-  int kbR, rbR1, rbR2, plR; // R side: first K block, row blocks of the two boxes, plane of slice 0
+  int kbR, rbR, plR;        // R side: first K block, first 64-row block, plane of slice 0
   int kblocks;
   const int* eRow;          // indexed by the tile's absolute row
   const int* eC0;           // column exponents of TMEM columns [0, 64) (+ column in strip)
@@ -436,18 +440,17 @@ template <int MODE>
 __device__ __forceinline__ SegInfo seg_info(const SplitParams& P, const TileId& t, int sg) {
   SegInfo si;
   if (is_contract(MODE)) {
-    // complex: B rows 0..63 from R' and 64..127 from R'' (same 64 columns);
-    // real: B rows = 128 consecutive columns of R'
+    // complex: B rows 0..63 from R' and 64..127 from R'' (same 64 columns: the R box
+    // is one row block of the interleaved plain / rotated planes); real: B rows = 128
+    // consecutive columns of R' (a box of two row blocks)
     const SplitSeg& S = P.seg[sg];
     si.mL = &P.maps[S.mL];
-    si.mR1 = &P.maps[S.mR];
-    si.mR2 = &P.maps[is_real(MODE) ? S.mR : S.mRr];
+    si.mR = &P.maps[S.mR];
     si.kbL = 0;
     si.rbL = t.i0 >> 6;
     si.plL = 0;
     si.kbR = 0;
-    si.rbR1 = t.j0 >> 6;
-    si.rbR2 = (t.j0 >> 6) + (is_real(MODE) ? 1 : 0);
+    si.rbR = t.j0 >> 6;
     si.plR = 0;
     si.kblocks = S.kblocks;
     si.eRow = S.eL;
@@ -457,14 +460,13 @@ __device__ __forceinline__ SegInfo seg_info(const SplitParams& P, const TileId& 
     const AtomsArgs& A = P.at;
     const AtomsReq& R = A.rq[t.r];
     si.mL = &P.maps[sg == 0 ? R.mA : R.mB];
-    si.mR1 = si.mR2 = &P.maps[A.mOp[t.job]];
+    si.mR = &P.maps[A.mOp[t.job]];
     const int pr = is_real(MODE) ? 1 : 2;  // real K positions per row
     si.kbL = (pr * t.a * A.N_L) / KB;  // atom a's rows in the packed layout
     si.rbL = t.i0 >> 6;
     si.plL = 0;
     si.kbR = sg * (A.P / KB);  // Z operator: A part in [0, P), B part in [P, 2P)
-    si.rbR1 = t.n0 >> 6;
-    si.rbR2 = (t.n0 >> 6) + 1;
+    si.rbR = t.n0 >> 6;
     si.plR = t.a * P.s;
     si.kblocks = (pr * (t.a + 1) * A.N_L + KB - 1) / KB - si.kbL;
     si.eRow = sg == 0 ? R.eA : R.eB;
@@ -547,8 +549,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
     for (int sg = 0; sg < T0.nseg; ++sg) {
       const SegInfo si = seg_info<MODE>(P, T0, sg);
       prefetch_map(si.mL);
-      prefetch_map(si.mR1);
-      prefetch_map(si.mR2);
+      prefetch_map(si.mR);
     }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
@@ -561,41 +562,33 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0) {
-    // ---------------- TMA producer: lane 0 waits for free stages and arms them;
-    // the stage's boxes are then issued by one lane each, in one warp instruction
-    constexpr int NB = 4;  // boxes per slice: the two 64-row halves of L', R', R''
+  if (warp == 0 && P.stall) {
+    // ---------------- stall injection (test only): nothing is armed and nothing is in
+    // flight, so the MMA thread's and the drain's bounded waits run out
+  } else if (warp == 0) {
+    // ---------------- TMA producer (lane 0): waits for a free stage, arms it and
+    // issues its two boxes, every slice of L' (A operand) and of R (B operand)
     int slot = 0;
     uint32_t phase = 0;
     uint32_t armed = 0;        // bit i: slot i was armed at least once
     uint32_t armed_par = 0;    // bit i: parity of the last armed phase of slot i
     bool ok = true;
-    const int bp = lane / NB, bk = lane - bp * NB;  // this lane's slice and box kind
+    if (lane == 0)
     for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
      const TileId T = decode_tile<MODE>(P, tile);
      for (int sg = 0; sg < T.nseg && ok; ++sg) {
       const SegInfo si = seg_info<MODE>(P, T, sg);
       for (int kb = 0; kb < si.kblocks; ++kb) {
-        if (lane == 0) {
-          ok = mbar_wait(&empty[slot], phase ^ 1u, abort_flag);
-          if (ok) mbar_expect_tx(&full[slot], stage_bytes);
-        }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
+        ok = mbar_wait(&empty[slot], phase ^ 1u, abort_flag);
         if (!ok) break;
+        mbar_expect_tx(&full[slot], stage_bytes);
         armed |= 1u << slot;
         armed_par = (armed_par & ~(1u << slot)) | (phase << slot);
         const uint32_t sa = smem_u32(smem + slot * stage_bytes);
-        const uint32_t sb = sa + a_bytes;
-        const int kl = si.kbL + kb, kr = si.kbR + kb;
-        if (bp < s) {
-          const uint32_t da = sa + bp * 2 * TILE_BYTES, db = sb + bp * 2 * TILE_BYTES;
-          if (bk == 0) tma_load_tile(da, si.mL, kl, si.rbL, si.plL + bp, &full[slot]);
-          else if (bk == 1)
-            tma_load_tile(da + TILE_BYTES, si.mL, kl, si.rbL + 1, si.plL + bp, &full[slot]);
-          else if (bk == 2) tma_load_tile(db, si.mR1, kr, si.rbR1, si.plR + bp, &full[slot]);
-          else tma_load_tile(db + TILE_BYTES, si.mR2, kr, si.rbR2, si.plR + bp, &full[slot]);
-        }
-        __syncwarp();
+        // A: [slice p][row half][64 rows][16] (slice p at p x 4 KB); B: [slice q][R' | R''
+        // or the two row halves][64 rows][16] (slice q at q x 4 KB); a_bytes each
+        tma_load_tile(sa, si.mL, si.kbL + kb, si.rbL, si.plL, &full[slot]);
+        tma_load_tile(sa + a_bytes, si.mR, si.kbR + kb, si.rbR, si.plR, &full[slot]);
         if (++slot == NS) {
           slot = 0;
           phase ^= 1u;
@@ -852,8 +845,9 @@ __device__ __forceinline__ size_t tile_off(int row, int j, int NKB) {
 struct SliceJob {
   const double2* X;  // source: nblk * N_L complex rows x N_G, column-major, ld ldX
   const double* u;   // optional real row weight (the U norms), may be null
-  uint16_t* plain;   // [s][rows_pad][kpad] BF16 slices of (re, im) pairs
-  uint16_t* rot;     // same for (im, -re) pairs, may be null
+  uint16_t* plain;   // [s][rows_pad][kpad] BF16 slices of (re, im) pairs, or with rot
+                     // [s][2][rows_pad][kpad]: (re, im) and (im, -re) slices interleaved
+  int rot;           // nonzero: also write the (im, -re) slices
   int* expo;         // [rows_pad] column exponents
   int ldX, nblk;
 };
@@ -922,9 +916,11 @@ __device__ __forceinline__ int slice_exponent(double mm) {
   return 0;
 }
 
-// Write the s slices of one complex entry (re, im): plain (re, im) and rotated (im, -re).
-__device__ __forceinline__ void put_slices(double2 v, bool zero, int E, int s, uint16_t* plain,
-                                           uint16_t* rot, size_t slice_elems, size_t off) {
+// Write the s slices of one complex entry (re, im): plain (re, im) at base + p pstride +
+// off and, with rot, rotated (im, -re) at base + rot_off + p pstride + off.
+__device__ __forceinline__ void put_slices(double2 v, bool zero, int E, int s, uint16_t* base,
+                                           bool rot, size_t pstride, size_t rot_off,
+                                           size_t off) {
   int dr[kMaxSlices], di[kMaxSlices];
   const bool bad = !zero && !(finite_bits(v.x) && finite_bits(v.y));
   if (!zero) {
@@ -946,8 +942,8 @@ __device__ __forceinline__ void put_slices(double2 v, bool zero, int E, int s, u
         pl = br | (bi << 16);
         rt = bi | ((br == 0u ? 0u : br ^ 0x8000u) << 16);  // -dr: sign flip (zero stays +0)
       }
-      *(uint32_t*)(plain + p * slice_elems + off) = pl;
-      if (rot) *(uint32_t*)(rot + p * slice_elems + off) = rt;
+      *(uint32_t*)(base + p * pstride + off) = pl;
+      if (rot) *(uint32_t*)(base + rot_off + p * pstride + off) = rt;
     }
   }
 }
@@ -959,6 +955,7 @@ __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SlicePara
   const int K = J.nblk * P.N_L;                  // complex rows of the source
   const int kpad = ((2 * K + KB - 1) / KB) * KB;  // packed real K, whole 16-wide blocks
   const size_t slice_elems = (size_t)P.rows_pad * kpad;
+  const size_t pstride = (J.rot ? 2 : 1) * slice_elems;  // plain slice p at p pstride
   __shared__ unsigned long long red[32];
   __shared__ int s_E;
   const int kc = kpad / 2;  // complex positions per padded row
@@ -966,8 +963,8 @@ __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SlicePara
   if (g >= P.N_G) {
     for (int k = threadIdx.x; k < kc; k += blockDim.x)
       for (int p = 0; p < s; ++p) {
-        *(uint32_t*)(J.plain + p * slice_elems + tile_off(g, k, NKB)) = 0u;
-        if (J.rot) *(uint32_t*)(J.rot + p * slice_elems + tile_off(g, k, NKB)) = 0u;
+        *(uint32_t*)(J.plain + p * pstride + tile_off(g, k, NKB)) = 0u;
+        if (J.rot) *(uint32_t*)(J.plain + slice_elems + p * pstride + tile_off(g, k, NKB)) = 0u;
       }
     if (threadIdx.x == 0) J.expo[g] = 0;
     return;
@@ -1001,7 +998,7 @@ __global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SlicePara
         v.y *= J.u[j];
       }
     }
-    put_slices(v, zero, E, s, J.plain, J.rot, slice_elems, tile_off(g, j, NKB));
+    put_slices(v, zero, E, s, J.plain, J.rot != 0, pstride, slice_elems, tile_off(g, j, NKB));
   }
 }
 
@@ -1053,7 +1050,7 @@ __global__ void __launch_bounds__(128) k_slice_op(const double2* __restrict__ M,
       const double2 mv = Ma[L + (size_t)(part * N_L + l) * ldM];
       v = c == 0 ? make_double2(mv.x, -mv.y) : make_double2(mv.y, mv.x);
     }
-    put_slices(v, zero, E, s, base, nullptr, slice_elems, tile_off(n, j, Kop / KB));
+    put_slices(v, zero, E, s, base, false, slice_elems, 0, tile_off(n, j, Kop / KB));
   }
 }
 
@@ -1103,7 +1100,7 @@ __global__ void __launch_bounds__(256) k_slice_real(const __grid_constant__ Slic
       if (k0 < K) x0 *= J.u[k0];
       if (k1 < K) x1 *= J.u[k1];
     }
-    put_slices(make_double2(x0, x1), k0 >= K, E, s, J.plain, nullptr, slice_elems,
+    put_slices(make_double2(x0, x1), k0 >= K, E, s, J.plain, false, slice_elems, 0,
                tile_off(g, j, NKB));
   }
 }
@@ -1147,7 +1144,7 @@ __global__ void __launch_bounds__(128) k_slice_op_real(const double2* __restrict
       const int part = q / P, l = q - part * P - oa;
       x[h] = (L < N_L && l >= 0 && l < N_L) ? Ma[L + (size_t)(part * N_L + l) * ldM].x : 0.0;
     }
-    put_slices(make_double2(x[0], x[1]), L >= N_L, E, s, base, nullptr, slice_elems,
+    put_slices(make_double2(x[0], x[1]), L >= N_L, E, s, base, false, slice_elems, 0,
                tile_off(L, j, Kop / KB));
   }
 }
@@ -1169,19 +1166,38 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 // Tensor map over a blocked slice array: dims (16 elements, 64 rows, NKB K blocks,
-// NRB row blocks, planes), one box = one contiguous 2 KB tile.
-bool encode_tiles(CUtensorMap* m, const uint16_t* base, int NKB, int NRB, int planes) {
+// NRB row blocks, planes `plane_tiles` tiles of 2 KB apart), box (16, 64, 1, box_rb,
+// box_planes): every (row block, plane) of a box is one contiguous 2 KB tile, so a box
+// lands in shared memory as [plane][row block] 2 KB tiles.
+bool encode_tiles(CUtensorMap* m, const uint16_t* base, int NKB, int NRB, int planes,
+                  size_t plane_tiles, int box_rb, int box_planes) {
   auto fn = get_encode();
   if (!fn) return false;
+  if (box_rb < 1 || box_rb > NRB || box_planes < 1 || box_planes > planes) return false;
   cuuint64_t dims[5] = {(cuuint64_t)KB, 64u, (cuuint64_t)NKB, (cuuint64_t)NRB, (cuuint64_t)planes};
   cuuint64_t strides[4] = {(cuuint64_t)KB * 2, (cuuint64_t)TILE_BYTES,
-                           (cuuint64_t)NKB * TILE_BYTES, (cuuint64_t)NRB * NKB * TILE_BYTES};
-  cuuint32_t box[5] = {(cuuint32_t)KB, 64u, 1u, 1u, 1u};
+                           (cuuint64_t)NKB * TILE_BYTES, (cuuint64_t)plane_tiles * TILE_BYTES};
+  cuuint32_t box[5] = {(cuuint32_t)KB, 64u, 1u, (cuuint32_t)box_rb, (cuuint32_t)box_planes};
   cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+// Maps over the slices of one operand source with NKB K blocks and NRB 64-row blocks.
+// A source with a rotated copy stores plain and rotated slices interleaved by plane
+// (plane 2p: slice p of (re, im) pairs, plane 2p + 1: slice p of (im, -re) pairs).
+//  * left role: the s plain slices of two row blocks (128 rows) per box;
+//  * right role, complex: the plain and rotated slices of one row block (64 columns)
+//    per box (2 s planes); right role, real: as the left role (128 columns).
+bool encode_left(CUtensorMap* m, const uint16_t* base, int NKB, int NRB, int s, bool rot) {
+  const size_t plane = (size_t)NRB * NKB * (rot ? 2 : 1);
+  return encode_tiles(m, base, NKB, NRB, s, plane, 2, s);
+}
+bool encode_right(CUtensorMap* m, const uint16_t* base, int NKB, int NRB, int s, bool rot) {
+  if (!rot) return encode_left(m, base, NKB, NRB, s, false);
+  return encode_tiles(m, base, NKB, NRB, 2 * s, (size_t)NRB * NKB, 1, 2 * s);
 }
 
 }  // namespace
@@ -1245,8 +1261,8 @@ int hs_plan_s::split_ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st
     bool rot;
     source_shape(src, N_A, n_fail, real, nblk, rot);
     const size_t one = (size_t)slices * rp * kpad_of(nblk, N_L, real) * 2;
-    if (!al((void**)&w.sb[src].plain, one)) return HS_ENOMEM;
-    if (rot && !al((void**)&w.sb[src].rot, one)) return HS_ENOMEM;
+    if (!al((void**)&w.sb[src].plain, (rot ? 2 : 1) * one)) return HS_ENOMEM;
+    w.sb[src].rot = rot;
     if (!al((void**)&w.sb[src].expo, sizeof(int) * rp)) return HS_ENOMEM;
   }
   return HS_OK;
@@ -1310,6 +1326,22 @@ template <int MODE, int S>
 static int launch_one(int grid, size_t smem, cudaStream_t st, const SplitParams& P) {
   int rc = set_smem((const void*)k_split_gemm<MODE, S>, smem);
   if (rc) return rc;
+  const char* e = std::getenv("HS_PAIR_CLUSTER");
+  if (is_contract(MODE) && e && e[0] == '1' && grid % 2 == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NUM_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_split_gemm<MODE, S>, P) == cudaSuccess ? HS_OK : HS_ECUDA;
+  }
   k_split_gemm<MODE, S><<<grid, NUM_THREADS, smem, st>>>(P);
   return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
 }
@@ -1327,8 +1359,21 @@ static int launch_mode(int s, int grid, size_t smem, cudaStream_t st, const Spli
   }
 }
 
+// Test-only stall injection (HS_TEST_STALL=1): every slice-GEMM launch arms no stage and
+// issues no copy, so its bounded waits give up (2 s) and the kernel sets the device error
+// word and returns (the host sees HS_EDEVICE).  Read at every launch.
+static bool stall_injection() {
+  const char* e = std::getenv("HS_TEST_STALL");
+  return e && e[0] == '1';
+}
+
+// The launch parameters as they go to the device: the stall flag.
+static void set_waits(SplitParams& P) { P.stall = stall_injection() ? 1 : 0; }
+
 static int launch_gemm(int mode, int s, int grid, size_t smem, cudaStream_t st,
-                       const SplitParams& P) {
+                       const SplitParams& P0) {
+  SplitParams P = P0;
+  set_waits(P);
   switch (mode) {
     case MODE_CONTRACT: return launch_mode<MODE_CONTRACT>(s, grid, smem, st, P);
     case MODE_ATOMS: return launch_mode<MODE_ATOMS>(s, grid, smem, st, P);
@@ -1371,7 +1416,9 @@ void hs_atoms_graph_free(AtomsGraph* a) {
 }
 
 static int graph_launch_atoms(AtomsGraph& G, int s, int grid, size_t smem, cudaStream_t st,
-                              const SplitParams& P) {
+                              const SplitParams& P0) {
+  SplitParams P = P0;
+  set_waits(P);
   const void* fn = atoms_fn(s);
   if (!fn) return HS_EINVAL;
   int rc = set_smem(fn, smem);
@@ -1396,27 +1443,35 @@ static int graph_launch_atoms(AtomsGraph& G, int s, int grid, size_t smem, cudaS
 }
 
 // ---------------------------------------------------------------- autotuner
-// Pipeline depth (TMA ring stages) of each kernel mode, tuned per (mode, slices,
-// N_L, N_G bucket of 1024): the first synchronous assembly with an untuned key
-// times every candidate depth on its real work (the trial launches compute the
-// same result as the final one) and keeps the fastest.  Serving requests use the
-// tuned value when there is one and the deepest ring otherwise.  HS_AUTOTUNE=0
-// disables tuning; HS_TUNE_CACHE=<file> loads and appends "key depth" lines.
+// Launch knobs tuned on the real work: the first synchronous assembly with an untuned
+// key times every candidate value (the trial launches compute the same result as the
+// final one) and keeps the fastest; a candidate other than the first must win by 2 %.
+//  * ring depth (TMA pipeline stages) of each kernel mode, key "mode:s:N_L:bucket";
+//  * the contraction's band width (row blocks per band of its tile order, which sets
+//    how compact the block of tiles resident at one time is and so the L2 reuse of
+//    the slice boxes), key "band:mode:s:N_L:bucket", candidates 8, 4, 16, 32;
+//  * the slicer's block size (threads per operand column), key
+//    "slice:real:s:N_L:bucket", candidates 256, 128.
+// bucket = N_G / 1024 rounded up.  Serving requests use tuned values when there are
+// some and the defaults otherwise.  HS_AUTOTUNE=0 disables tuning; HS_TUNE_CACHE=<file>
+// loads (whenever the name changes) and appends "key value" lines.  The per-atom kernel's grid is not a knob: its
+// ring fills an SM's shared memory, so it runs one CTA per SM by construction.
 namespace {
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
-bool g_tune_loaded = false;
+std::string g_tune_path;  // the HS_TUNE_CACHE file read last ("" = none yet)
 
 std::string tune_key(int mode, int s, int N_L, int N_G) {
   return std::to_string(mode) + ":" + std::to_string(s) + ":" + std::to_string(N_L) + ":" +
          std::to_string((N_G + 1023) / 1024);
 }
 
+// Reads the cache file named by HS_TUNE_CACHE whenever that name changes (its values
+// override the ones in memory).
 void tune_load_locked() {
-  if (g_tune_loaded) return;
-  g_tune_loaded = true;
   const char* path = std::getenv("HS_TUNE_CACHE");
-  if (!path) return;
+  if (!path || g_tune_path == path) return;
+  g_tune_path = path;
   std::FILE* f = std::fopen(path, "r");
   if (!f) return;
   char key[128];
@@ -1440,37 +1495,42 @@ size_t smem_for(int mode, int n_stage, int stage_bytes) {
   return (is_contract(mode) ? std::max(ring, (size_t)STAGING_CONTRACT) : ring) + 1024 + 256;
 }
 
-// Depth for this launch; `trial(depth)` enqueues the real work with that depth.
-int tuned_depth(int mode, int s, int N_L, int N_G, int max_depth, bool allow, cudaStream_t st,
-                const std::function<int(int)>& trial) {
-  const std::string key = tune_key(mode, s, N_L, N_G);
+// The cached value of `key` if any; else, when tuning is allowed, the fastest of
+// `cand` (cand[0] is the default) timed with `trial(value)`, which enqueues the real
+// work; else cand[0].  `found` tells whether the value came from the cache.
+int tuned_choice(const std::string& key, const std::vector<int>& cand, bool allow,
+                 cudaStream_t st, const std::function<int(int)>& trial, bool* found = nullptr) {
+  if (found) *found = false;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_load_locked();
     auto it = g_tune.find(key);
-    if (it != g_tune.end()) return std::min(std::max(it->second, 2), max_depth);
+    if (it != g_tune.end()) {
+      if (found) *found = true;
+      return it->second;
+    }
   }
   const char* env = std::getenv("HS_AUTOTUNE");
-  if (!allow || (env && env[0] == '0')) return max_depth;
+  if (!allow || cand.size() < 2 || (env && env[0] == '0') || stall_injection()) return cand[0];
   cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess) return max_depth;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cand[0];
   if (cudaEventCreate(&e1) != cudaSuccess) {
     cudaEventDestroy(e0);
-    return max_depth;
+    return cand[0];
   }
-  int best = max_depth;
+  int best = cand[0];
   float best_ms = 1e30f;
-  for (int d = max_depth; d >= 2; --d) {
+  for (int v : cand) {
     float ms = 0.f;
-    if (cudaEventRecord(e0, st) != cudaSuccess || trial(d) != HS_OK ||
+    if (cudaEventRecord(e0, st) != cudaSuccess || trial(v) != HS_OK ||
         cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
       cudaGetLastError();
       break;
     }
-    if (ms < 0.98f * best_ms) {  // a shallower ring must win clearly
+    if (ms < 0.98f * best_ms) {  // a later candidate must win clearly
       best_ms = ms;
-      best = d;
+      best = v;
     }
   }
   cudaEventDestroy(e0);
@@ -1479,17 +1539,51 @@ int tuned_depth(int mode, int s, int N_L, int N_G, int max_depth, bool allow, cu
   tune_store_locked(key, best);
   return best;
 }
+
+// Depth for this launch; `trial(depth)` enqueues the real work with that depth.
+int tuned_depth(int mode, int s, int N_L, int N_G, int max_depth, bool allow, cudaStream_t st,
+                const std::function<int(int)>& trial) {
+  std::vector<int> cand;
+  for (int d = max_depth; d >= 2; --d) cand.push_back(d);
+  const int v = tuned_choice(tune_key(mode, s, N_L, N_G), cand, allow, st, trial);
+  return std::min(std::max(v, 2), max_depth);
+}
 }  // namespace
 
-// Row blocks per band of the contraction's tile order: 8 (152 resident CTAs
-// then span about 8 row blocks x 19 column blocks); HS_BAND overrides.
-static int contract_band() {
+// Row blocks per band of the contraction's tile order: tuned per key (8 by default:
+// 152 resident CTAs then span about 8 row blocks x 19 column blocks); HS_BAND > 0 fixes it.
+static int band_override() {
   static const int band = []() {
     const char* e = std::getenv("HS_BAND");
     const int v = e ? std::atoi(e) : 0;
-    return v >= 1 ? v : 8;
+    return v >= 1 ? v : 0;
   }();
   return band;
+}
+static int contract_band(int mode = 0, int s = 0, int N_L = 0, int N_G = 0) {
+  if (band_override()) return band_override();
+  if (s == 0) return 8;
+  bool found = false;
+  const int v = tuned_choice("band:" + tune_key(mode, s, N_L, N_G), {8}, false, nullptr,
+                             [](int) { return HS_OK; }, &found);
+  return found && v >= 1 ? v : 8;
+}
+static int tuned_band(int mode, int s, int N_L, int N_G, bool allow, cudaStream_t st,
+                      const std::function<int(int)>& trial) {
+  if (band_override()) return band_override();
+  const int v = tuned_choice("band:" + tune_key(mode, s, N_L, N_G), {8, 4, 16, 32}, allow, st,
+                             trial);
+  return v >= 1 ? v : 8;
+}
+
+// Threads per slicer block (one block per operand column).
+static int slice_threads(bool real, int s, int N_L, int N_G, bool allow, cudaStream_t st,
+                         const std::function<int(int)>& trial) {
+  const int v = tuned_choice("slice:" + std::to_string(real ? 1 : 0) + ":" + std::to_string(s) +
+                                 ":" + std::to_string(N_L) + ":" +
+                                 std::to_string((N_G + 1023) / 1024),
+                             {256, 128}, allow, st, trial);
+  return v == 128 ? v : 256;
 }
 
 int hs_plan_s::split_geometry(int& n_stage, size_t& smem) const {
@@ -1509,23 +1603,25 @@ static void slice_job(SliceParams& sp, int& nj, Workspace& w, int src, const dou
 }
 
 static int slice_launch(SliceParams& sp, int nj, int s, int N_G, int rp, int N_L, bool real,
-                        cudaStream_t st, int g0 = 0, int ng = -1) {
+                        cudaStream_t st, int g0 = 0, int ng = -1, int threads = 256) {
   if (ng < 0) ng = rp - g0;
   if (g0 < 0 || ng < 0 || g0 + ng > rp) return HS_EINVAL;
   if (ng == 0) return HS_OK;  // nothing left to slice
+  if (threads != 128 && threads != 256) return HS_EINVAL;
   sp.g0 = g0;
   sp.s = s;
   sp.N_G = N_G;
   sp.rows_pad = rp;
   sp.N_L = N_L;
-  if (real) k_slice_real<<<dim3(ng, nj), 256, 0, st>>>(sp);
-  else k_slice<<<dim3(ng, nj), 256, 0, st>>>(sp);
+  if (real) k_slice_real<<<dim3(ng, nj), threads, 0, st>>>(sp);
+  else k_slice<<<dim3(ng, nj), threads, 0, st>>>(sp);
   return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
 }
 
-// 1. slice the inputs A, U.B, B of one k-point
+// 1. slice the inputs A, U.B, B of one k-point (tune: time the slicer's block sizes on
+//    this work if its key is untuned)
 int hs_plan_s::split_inputs(const double2* A, const double2* B, int ldAB, const double* U,
-                            int N_G, Workspace& w, cudaStream_t st, int g0, int ng) {
+                            int N_G, Workspace& w, cudaStream_t st, int g0, int ng, bool tune) {
   const int rp = rows_pad_of(N_G, real);
   if (rows_pad_of(w.N_G, real) < rp || w.n_fail < N_f || !w.sb[SRC_A].plain) return HS_EINVAL;
   SliceParams sp{};
@@ -1533,7 +1629,12 @@ int hs_plan_s::split_inputs(const double2* A, const double2* B, int ldAB, const 
   slice_job(sp, nj, w, SRC_A, A, ldAB, N_A, nullptr);
   slice_job(sp, nj, w, SRC_UB, B, ldAB, N_A, U);
   slice_job(sp, nj, w, SRC_B, B, ldAB, N_A, nullptr);
-  return slice_launch(sp, nj, slices, N_G, rp, N_L, real, st, g0, ng);
+  const int threads = slice_threads(real, slices, N_L, N_G, tune && g0 == 0 && ng < 0, st,
+                                    [&](int t) {
+                                      return slice_launch(sp, nj, slices, N_G, rp, N_L, real, st,
+                                                          g0, ng, t);
+                                    });
+  return slice_launch(sp, nj, slices, N_G, rp, N_L, real, st, g0, ng, threads);
 }
 
 // 2. per-atom products of up to kMaxBatch k-points in one grouped launch: Z and
@@ -1551,8 +1652,11 @@ int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGr
   if (!PA) return HS_ENOMEM;
   std::memset(PA, 0, sizeof(*PA));
   AtomsArgs& at = PA->at;
-  bool ok = encode_tiles(&PA->maps[0], op_slices[0], 2 * Pp / KB, np / 64, N_A * s) &&
-            encode_tiles(&PA->maps[1], op_slices[1], Pp / KB, np / 64, N_A * s);
+  // operator slices [a][p][n_pad][Kop]: the right operand, two row blocks x s planes
+  bool ok = encode_tiles(&PA->maps[0], op_slices[0], 2 * Pp / KB, np / 64, N_A * s,
+                         (size_t)(np / 64) * (2 * Pp / KB), 2, s) &&
+            encode_tiles(&PA->maps[1], op_slices[1], Pp / KB, np / 64, N_A * s,
+                         (size_t)(np / 64) * (Pp / KB), 2, s);
   at.mOp[0] = 0;
   at.mOp[1] = 1;
   int grid = 0;
@@ -1563,8 +1667,8 @@ int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGr
     R.mA = 2 + 2 * r;
     R.mB = 3 + 2 * r;
     const int nkb = kpad_of(N_A, N_L, real) / KB;
-    ok = encode_tiles(&PA->maps[R.mA], w.sb[SRC_A].plain, nkb, rp / 64, s) &&
-         encode_tiles(&PA->maps[R.mB], w.sb[SRC_B].plain, nkb, rp / 64, s);
+    ok = encode_left(&PA->maps[R.mA], w.sb[SRC_A].plain, nkb, rp / 64, s, w.sb[SRC_A].rot) &&
+         encode_left(&PA->maps[R.mB], w.sb[SRC_B].plain, nkb, rp / 64, s, w.sb[SRC_B].rot);
     R.eA = w.sb[SRC_A].expo;
     R.eB = w.sb[SRC_B].expo;
     R.Z = w.Z;
@@ -1646,7 +1750,8 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
                               : w.W2 + (size_t)N_h * N_L;
       slice_job(sp, nj, w, SRC_X, X, K, N_f, nullptr);
     }
-    rc = slice_launch(sp, nj, s, N_G, rp, N_L, real, st);
+    const int threads = slice_threads(real, s, N_L, N_G, false, st, [](int) { return HS_OK; });
+    rc = slice_launch(sp, nj, s, N_G, rp, N_L, real, st, 0, -1, threads);
     if (rc) return rc;
   }
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[5], st));
@@ -1657,18 +1762,13 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   std::memset(&P, 0, sizeof(P));
   int map_of[NSRC][2];
   int nm = 0;
-  auto add_map = [&](int src, int nblk) -> bool {
+  auto add_map = [&](int src, int nblk) -> bool {  // [0]: left role, [1]: right role
     SliceBuf& b = w.sb[src];
+    const int nkb = kpad_of(nblk, N_L, real) / KB;
     map_of[src][0] = nm;
-    if (!encode_tiles(&P.maps[nm++], b.plain, kpad_of(nblk, N_L, real) / KB, rp / 64, s))
-      return false;
-    map_of[src][1] = map_of[src][0];  // real plans: no rotated copy
-    if (b.rot) {
-      map_of[src][1] = nm;
-      if (!encode_tiles(&P.maps[nm++], b.rot, kpad_of(nblk, N_L, real) / KB, rp / 64, s))
-        return false;
-    }
-    return true;
+    if (!encode_left(&P.maps[nm++], b.plain, nkb, rp / 64, s, b.rot)) return false;
+    map_of[src][1] = nm;
+    return encode_right(&P.maps[nm++], b.plain, nkb, rp / 64, s, b.rot);
   };
   bool ok = add_map(SRC_A, N_A) && add_map(SRC_UB, N_A) && add_map(SRC_Z, N_A) &&
             add_map(SRC_B, N_A);
@@ -1690,13 +1790,12 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   for (int b = 0; b < nbi; ++b)  // CTA pairs: column pair c from row block c (2c if real)
     tiles += 2 * std::min((real ? b / 2 : b) + 1, (P.nbj + 1) / 2);
   P.nbi = nbi;
-  P.band = contract_band();
+  P.band = contract_band(mode, s, N_L, N_G);
   P.ntiles = tiles;  // one tile per CTA
   auto seg = [&](int srcL, int srcR, int nblk) {
     SplitSeg g;
     g.mL = map_of[srcL][0];
-    g.mR = map_of[srcR][0];
-    g.mRr = map_of[srcR][1];
+    g.mR = map_of[srcR][1];
     g.kblocks = kpad_of(nblk, N_L, real) / KB;
     g.eL = w.sb[srcL].expo;
     g.eR = w.sb[srcR].expo;
@@ -1715,6 +1814,10 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
     });
     P.n_stage = depth;
     smem = smem_for(mode, depth, stage_bytes);
+    P.band = tuned_band(mode, s, N_L, N_G, timed, st, [&](int b) {
+      P.band = b;
+      return launch_gemm(mode, s, tiles, smem, st, P);
+    });
   }
   if (!skip_S) rc = launch_gemm(mode, s, tiles, smem, st, P);
   if (rc == HS_OK && !skip_S && mirror) {  // S is final once mirrored: it can leave while H runs
@@ -1764,12 +1867,11 @@ int hs_plan_s::split_contract_S_rows(int N_G, double2* S, Workspace& w, cudaStre
   bool ok = true;
   for (int i = 0; i < 2 && ok; ++i) {
     SliceBuf& b = w.sb[i == 0 ? SRC_A : SRC_UB];
-    map_of[i][0] = map_of[i][1] = nm;
-    ok = encode_tiles(&P.maps[nm++], b.plain, kpad_of(N_A, N_L, real) / KB, rp / 64, s);
-    if (ok && b.rot) {
-      map_of[i][1] = nm;
-      ok = encode_tiles(&P.maps[nm++], b.rot, kpad_of(N_A, N_L, real) / KB, rp / 64, s);
-    }
+    const int nkb = kpad_of(N_A, N_L, real) / KB;
+    map_of[i][0] = nm;
+    ok = encode_left(&P.maps[nm++], b.plain, nkb, rp / 64, s, b.rot);
+    map_of[i][1] = nm;
+    ok = ok && encode_right(&P.maps[nm++], b.plain, nkb, rp / 64, s, b.rot);
   }
   if (!ok) {
     delete PP;
@@ -1785,13 +1887,12 @@ int hs_plan_s::split_contract_S_rows(int N_G, double2* S, Workspace& w, cudaStre
   for (int b = bi0; b < bi1; ++b) tiles += 2 * std::min((real ? b / 2 : b) + 1, (P.nbj + 1) / 2);
   P.bi0 = bi0;
   P.nbi = bi1;
-  P.band = contract_band();
+  P.band = contract_band(mode, s, N_L, N_G);
   P.ntiles = tiles;
   for (int i = 0; i < 2; ++i) {
     SplitSeg& g = P.seg[i];
     g.mL = map_of[i][0];
-    g.mR = map_of[i][0];
-    g.mRr = map_of[i][1];
+    g.mR = map_of[i][1];
     g.kblocks = kpad_of(N_A, N_L, real) / KB;
     g.eL = g.eR = w.sb[i == 0 ? SRC_A : SRC_UB].expo;
   }
@@ -1807,7 +1908,7 @@ int hs_plan_s::split_contract_S_rows(int N_G, double2* S, Workspace& w, cudaStre
 int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const double* U,
                              int N_G, double2* H, double2* S, Workspace& w, cudaStream_t st,
                              bool timed, cudaEvent_t s_done, bool presliced, bool mirror) {
-  int rc = presliced ? HS_OK : split_inputs(A, B, ldAB, U, N_G, w, st);
+  int rc = presliced ? HS_OK : split_inputs(A, B, ldAB, U, N_G, w, st, 0, -1, timed);
   if (rc) return rc;
   if (timed) HS_CUDA_TRY(cudaEventRecord(ev[9], st));
   AtomsJob job{&w, N_G};
@@ -1829,7 +1930,6 @@ int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const
 void hs_plan_s::split_reduce_release() {
   for (SliceBuf* b : {&red_M, &red_Zs, &red_M2}) {
     if (b->plain) cudaFree(b->plain);
-    if (b->rot) cudaFree(b->rot);
     if (b->expo) cudaFree(b->expo);
     *b = SliceBuf{};
   }
@@ -1854,19 +1954,15 @@ int hs_plan_s::split_reduce_alloc(int n) {
   const size_t kpad = (size_t)kpad_of(n, 1);
   const size_t oneM = (size_t)slices * rpM * kpad * 2, oneZ = (size_t)slices * rp * kpad * 2;
   const bool ok =
-      cudaMalloc((void**)&red_M.plain, oneM) == cudaSuccess &&
-      cudaMalloc((void**)&red_M.rot, oneM) == cudaSuccess &&
+      cudaMalloc((void**)&red_M.plain, 2 * oneM) == cudaSuccess &&
       cudaMalloc((void**)&red_M.expo, sizeof(int) * rpM) == cudaSuccess &&
-      cudaMalloc((void**)&red_Zs.plain, oneZ) == cudaSuccess &&
-      cudaMalloc((void**)&red_Zs.rot, oneZ) == cudaSuccess &&
+      cudaMalloc((void**)&red_Zs.plain, 2 * oneZ) == cudaSuccess &&
       cudaMalloc((void**)&red_Zs.expo, sizeof(int) * rp) == cudaSuccess &&
       cudaMalloc((void**)&red_Z, sizeof(double2) * (size_t)n * NM) == cudaSuccess &&
       cudaMalloc((void**)&red_half, sizeof(double) * (size_t)n) == cudaSuccess &&
       // the inverse's scratch: slices of K <= kRedPanel over up to n_pad + n columns,
       // a kRedPanel x n transposed block, an n x (n_pad + n) product
-      cudaMalloc((void**)&red_M2.plain, (size_t)slices * rpM * kpad_of(kRedPanel, 1) * 2) ==
-          cudaSuccess &&
-      cudaMalloc((void**)&red_M2.rot, (size_t)slices * rpM * kpad_of(kRedPanel, 1) * 2) ==
+      cudaMalloc((void**)&red_M2.plain, (size_t)2 * slices * rpM * kpad_of(kRedPanel, 1) * 2) ==
           cudaSuccess &&
       cudaMalloc((void**)&red_M2.expo, sizeof(int) * rpM) == cudaSuccess &&
       cudaMalloc((void**)&red_P2, sizeof(double2) * (size_t)kRedPanel * n) == cudaSuccess &&
@@ -1888,6 +1984,7 @@ int hs_plan_s::split_reduce_alloc(int n) {
       split_reduce_release();
       return HS_ECUDA;
     }
+  red_M.rot = red_Zs.rot = red_M2.rot = true;  // plain and rotated slices interleaved
   red_split_cap = n;
   return HS_OK;
 }
@@ -1931,10 +2028,10 @@ int hs_plan_s::split_reduce_transform(const double2* B, double2* H, int n, cudaS
   SplitParams& P = *PP;
   // 2. H B: row blocks of M's H part against every column block up to the diagonal
   std::memset(&P, 0, sizeof(P));
-  if (!encode_tiles(&P.maps[0], red_M.plain, NKB, rpM / 64, s) ||
-      !encode_tiles(&P.maps[1], red_M.rot, NKB, rpM / 64, s))
+  if (!encode_left(&P.maps[0], red_M.plain, NKB, rpM / 64, s, true) ||
+      !encode_right(&P.maps[1], red_M.plain, NKB, rpM / 64, s, true))
     return HS_ECUDA;
-  P.seg[0] = SplitSeg{0, 0, 1, NKB, red_M.expo, red_M.expo};
+  P.seg[0] = SplitSeg{0, 1, NKB, red_M.expo, red_M.expo};
   P.nseg = 1;
   P.s = s;
   P.N_G = NM;
@@ -1960,13 +2057,13 @@ int hs_plan_s::split_reduce_transform(const double2* B, double2* H, int n, cudaS
   }
   // 4. C = Z^H B + B^H Z, lower tiles, into H; then the mirror
   std::memset(&P, 0, sizeof(P));
-  if (!encode_tiles(&P.maps[0], red_Zs.plain, NKB, rp / 64, s) ||
-      !encode_tiles(&P.maps[1], red_Zs.rot, NKB, rp / 64, s) ||
-      !encode_tiles(&P.maps[2], red_M.plain, NKB, rpM / 64, s) ||
-      !encode_tiles(&P.maps[3], red_M.rot, NKB, rpM / 64, s))
+  if (!encode_left(&P.maps[0], red_Zs.plain, NKB, rp / 64, s, true) ||
+      !encode_right(&P.maps[1], red_Zs.plain, NKB, rp / 64, s, true) ||
+      !encode_left(&P.maps[2], red_M.plain, NKB, rpM / 64, s, true) ||
+      !encode_right(&P.maps[3], red_M.plain, NKB, rpM / 64, s, true))
     return HS_ECUDA;
-  P.seg[0] = SplitSeg{0, 2, 3, NKB, red_Zs.expo, red_M.expo};  // Z^H B
-  P.seg[1] = SplitSeg{2, 0, 1, NKB, red_M.expo, red_Zs.expo};  // B^H Z
+  P.seg[0] = SplitSeg{0, 3, NKB, red_Zs.expo, red_M.expo};  // Z^H B
+  P.seg[1] = SplitSeg{2, 1, NKB, red_M.expo, red_Zs.expo};  // B^H Z
   P.nseg = 2;
   P.s = s;
   P.N_G = n;
@@ -2008,10 +2105,10 @@ int hs_plan_s::split_herk_lower(const double2* X, int ldX, int K, int nc, double
   std::unique_ptr<SplitParams> own(PP);
   SplitParams& P = *PP;
   std::memset(&P, 0, sizeof(P));
-  if (!encode_tiles(&P.maps[0], sb.plain, NKB, rp / 64, s) ||
-      !encode_tiles(&P.maps[1], sb.rot, NKB, rp / 64, s))
+  if (!encode_left(&P.maps[0], sb.plain, NKB, rp / 64, s, sb.rot) ||
+      !encode_right(&P.maps[1], sb.plain, NKB, rp / 64, s, sb.rot))
     return HS_ECUDA;
-  P.seg[0] = SplitSeg{0, 0, 1, NKB, sb.expo, sb.expo};
+  P.seg[0] = SplitSeg{0, 1, NKB, sb.expo, sb.expo};
   P.nseg = 1;
   P.s = s;
   P.N_G = nc;
@@ -2054,10 +2151,10 @@ int hs_plan_s::split_gemm_ahb(const double2* A, int ldA, int m, const double2* B
   std::unique_ptr<SplitParams> own(PP);
   SplitParams& P = *PP;
   std::memset(&P, 0, sizeof(P));
-  if (!encode_tiles(&P.maps[0], sb.plain, NKB, rpM / 64, s) ||
-      !encode_tiles(&P.maps[1], sb.rot, NKB, rpM / 64, s))
+  if (!encode_left(&P.maps[0], sb.plain, NKB, rpM / 64, s, sb.rot) ||
+      !encode_right(&P.maps[1], sb.plain, NKB, rpM / 64, s, sb.rot))
     return HS_ECUDA;
-  P.seg[0] = SplitSeg{0, 0, 1, NKB, sb.expo, sb.expo};
+  P.seg[0] = SplitSeg{0, 1, NKB, sb.expo, sb.expo};
   P.nseg = 1;
   P.s = s;
   P.N_G = NM;

@@ -19,11 +19,13 @@ constexpr int kMaxSlices = 7;  // 7 + 9*(s-1) bits must fit an int64 digit word
 constexpr int kRedPanel = 128;  // hs_reduce, split plans: FP64 panel width
 
 // Slice buffers of one operand source: s BF16 arrays [p][rows_pad][kpad] of
-// (re, im) pairs, optionally the same for (im, -re) pairs, and one exponent
-// per row (= column of the operand).
+// (re, im) pairs and one exponent per row (= column of the operand).  With `rot`
+// the same buffer also holds the slices of the (im, -re) pairs, interleaved by
+// plane: plane 2p = plain slice p, plane 2p + 1 = rotated slice p (one 2 KB TMA
+// tile row of the right operand then covers both).
 struct SliceBuf {
   uint16_t* plain = nullptr;
-  uint16_t* rot = nullptr;
+  bool rot = false;
   int* expo = nullptr;
 };
 // Operand sources of the two contractions.
@@ -149,7 +151,7 @@ struct hs_plan_s {
   // g0, ng: slice only operand columns [g0, g0 + ng) (ng < 0: every column and the zero
   // rows up to the padded row count)
   int split_inputs(const double2* A, const double2* B, int ldAB, const double* U, int N_G,
-                   Workspace& w, cudaStream_t st, int g0 = 0, int ng = -1);
+                   Workspace& w, cudaStream_t st, int g0 = 0, int ng = -1, bool tune = false);
   int split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGraph* graph);
   // also mirrors S (right after its contraction, then records s_done if given);
   // skip_S: S was already contracted and mirrored by the caller

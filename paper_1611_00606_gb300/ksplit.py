@@ -73,10 +73,17 @@ class KSplitPlan:
         return hs.hs_assemble_partial(self.plan.h, A[r], B[r], T_AA[a0:a1], T_AB[a0:a1],
                                       T_BB[a0:a1], U[a0:a1], a1 - a0, N_L, N_G, H, S)
 
+    def set_t(self, T_AA, T_AB, T_BB) -> None:
+        """Re-factorise this rank's T^AA blocks (after T changed in place)."""
+        from . import hs
+        a0, a1 = self.a0, self.a1
+        hs.hs_set_t(self.plan.h, T_AA[a0:a1], T_AB[a0:a1], T_BB[a0:a1])
+
     def assemble(self, A, B, T_AA, T_AB, T_BB, U, N_G: int, H, S, group=None) -> dict:
         from . import hs
         info = self.partial(A, B, T_AA, T_AB, T_BB, U, N_G, H, S)
-        sum_over_ranks(H, S, group)
+        if self.a1 - self.a0 < self.N_A:  # more than one range: add the partials up
+            sum_over_ranks(H, S, group)
         hs.hs_finalize(self.plan.h, H, S, N_G)
         return info
 

@@ -31,6 +31,14 @@ unitary factor of the QR of an ``n x n`` complex normal draw and ``s`` log-space
 from ``1/cond`` to 1, ``H = (N + N^H) / 2`` with ``N`` complex normal (tensor ids
 20, 21), both symmetrised exactly.
 
+Device draws (``make_inputs_device``, for the benchmark's large shapes, where
+drawing 14 GB of coefficients on the host would take a minute): A and B with the
+same distribution (``torch.randn`` complex128 gives re, im ~ N(0, 1/2); rows scaled
+by ``1 / (1 + l)``) from torch's counter-based (Philox) CUDA generator seeded with
+``seed * 1000003 + tensor id``; T and U from the host recipe above.  A different
+stream from the host draws, so the values differ; the shapes, distributions and
+structure are the same.
+
 Indefinite atoms: ``n_f = round(frac * N_A)`` atoms at
 ``(3 + floor(i * N_A / n_f)) mod N_A`` for ``i < n_f``.
 
@@ -234,6 +242,30 @@ def reduce_inputs(n: int, seed: int = 0, cond: float = 1e3):
     S = _herm((Q * s) @ Q.conj().T)
     H = _herm(_cnormal(_rng(seed, _ID_RH), (n, n)))
     return np.asfortranarray(H), np.asfortranarray(S)
+
+
+def coefficients_device(N_A: int, N_L: int, N_G: int, device, seed: int = 0,
+                        tid: int = _ID_A):
+    """A complex (K, N_G) column-major CUDA tensor (strides (1, K)) drawn on the device
+    with the coefficient recipe (complex normal, rows scaled by 1 / (1 + l))."""
+    import torch
+    K = N_A * N_L
+    g = torch.Generator(device=device)
+    g.manual_seed(seed * 1_000_003 + tid)
+    x = torch.randn((N_G, K), generator=g, device=device, dtype=torch.complex128)
+    rowscale = torch.from_numpy(np.tile(1.0 / (1.0 + l_of_L(N_L).astype(np.float64)), N_A))
+    x.mul_(rowscale.to(device)[None, :])
+    return x.T
+
+
+def make_inputs_device(w: Workload, device):
+    """Inputs of workload ``w`` with A, B drawn on ``device`` (see the module notes);
+    T_AA, T_AB, T_BB (N_A, N_L, N_L) and U (N_A, N_L) as numpy arrays (host recipe)."""
+    A = coefficients_device(w.N_A, w.N_L, w.N_G, device, w.seed, _ID_A)
+    B = coefficients_device(w.N_A, w.N_L, w.N_G, device, w.seed, _ID_B)
+    T_AA, T_AB, T_BB = t_matrices(w.N_A, w.N_L, w.indefinite, w.seed)
+    U = u_norms(w.N_A, w.N_L, w.seed)
+    return dict(A=A, B=B, T_AA=T_AA, T_AB=T_AB, T_BB=T_BB, U=U)
 
 
 def as_colmajor_T(T: np.ndarray) -> np.ndarray:

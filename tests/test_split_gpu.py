@@ -148,35 +148,42 @@ def test_error_table_split_8000(hs):
     assert max(max(table[s][:2]) for s in (6, 7)) <= min(1e-11, max(table[5][:2]))
 
 
-def test_split_large_12000_panels(hs):
-    """large_12000 (N_A=256, N_L=144, N_G=12000, 5 indefinite): the largest shape, on
-    oracle column panels at the start, middle and end."""
-    w = synth.WORKLOADS["large_12000"]
-    d = synth.make_inputs(w)
-    H, S, info, flags = _run(hs, d, w.N_A, w.N_L)
-    cols = _panel_cols(w.N_G)
-    Hr, Sr = assemble(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], w.N_A, w.N_L,
-                      cols=cols)
-    eh, es = rel_frobenius(H[:, cols], Hr), rel_frobenius(S[:, cols], Sr)
-    print(f"large_12000 split s=5: H {eh:.3e} S {es:.3e}  {info['ms_total']:.1f} ms")
-    assert eh <= TOL_SPLIT and es <= TOL_SPLIT
-    assert list(np.nonzero(flags)[0]) == list(w.indefinite)
-    assert np.array_equal(H[:, cols].conj().T[:, cols], H[np.ix_(cols, cols)])
-
-
 def test_autotuner_tunes_once_and_caches(hs, tmp_path, monkeypatch):
     """The first assembly of a new (mode, slices, N_L, N_G bucket) key times every
-    pipeline depth and records the fastest; later calls reuse it, bit for bit."""
+    candidate of each knob -- ring depth of both kernel modes, the contraction's band
+    width, the slicer's block size -- and records the fastest; later calls reuse them,
+    bit for bit, and tune nothing again."""
     path = tmp_path / "tune.txt"
     monkeypatch.setenv("HS_TUNE_CACHE", str(path))
     d = synth.make_inputs(synth.Workload("t", 3, 7, 700, (1,), seed=41))  # fresh N_L = 7 keys
     H1, S1, _, _ = _run(hs, d, 3, 7)
     words = path.read_text().split()
-    keys, depths = words[0::2], [int(v) for v in words[1::2]]
-    assert sorted(k.split(":")[0] for k in keys) == ["0", "1"]  # contraction and per-atom
-    assert all(2 <= v <= 8 for v in depths)
+    keys, vals = words[0::2], [int(v) for v in words[1::2]]
+    kv = dict(zip(keys, vals))
+    assert len(kv) == len(keys) == 4
+    assert kv["0:5:7:1"] in range(2, 9) and kv["1:5:7:1"] in range(2, 9)  # ring depths
+    assert kv["band:0:5:7:1"] in (4, 8, 16, 32)
+    assert kv["slice:0:5:7:1"] in (128, 256)
     H2, S2, _, _ = _run(hs, d, 3, 7)
     assert np.array_equal(H1, H2) and np.array_equal(S1, S2)
     assert len(path.read_text().split()) == len(words)  # nothing re-tuned
     Hr, Sr = assemble(d["A"], d["B"], d["T_AA"], d["T_AB"], d["T_BB"], d["U"], 3, 7)
     assert rel_frobenius(H1, Hr) <= TOL_SPLIT and rel_frobenius(S1, Sr) <= TOL_SPLIT
+
+
+def test_tuned_values_from_the_cache_file_are_used(hs, tmp_path, monkeypatch):
+    """A cache file written beforehand decides the knobs: any recorded band and slicer
+    block size give the same H and S (the tile order and the slicer's block shape do
+    not change the arithmetic)."""
+    d = synth.make_inputs(synth.Workload("t", 2, 6, 520, (), seed=42))  # fresh N_L = 6 keys
+    outs = []
+    for band, threads, depth in ((8, 256, 5), (4, 128, 3), (32, 256, 2)):
+        path = tmp_path / f"tune_{band}.txt"
+        path.write_text(f"0:5:6:1 {depth}\n1:5:6:1 {depth}\nband:0:5:6:1 {band}\n"
+                        f"slice:0:5:6:1 {threads}\n")
+        monkeypatch.setenv("HS_TUNE_CACHE", str(path))
+        H, S, _, _ = _run(hs, d, 2, 6)
+        outs.append((H, S))
+        assert len(path.read_text().split()) == 8  # read, not re-tuned
+    for H, S in outs[1:]:
+        assert np.array_equal(H, outs[0][0]) and np.array_equal(S, outs[0][1])
