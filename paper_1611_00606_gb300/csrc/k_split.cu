@@ -1326,22 +1326,6 @@ template <int MODE, int S>
 static int launch_one(int grid, size_t smem, cudaStream_t st, const SplitParams& P) {
   int rc = set_smem((const void*)k_split_gemm<MODE, S>, smem);
   if (rc) return rc;
-  const char* e = std::getenv("HS_PAIR_CLUSTER");
-  if (is_contract(MODE) && e && e[0] == '1' && grid % 2 == 0) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(NUM_THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_split_gemm<MODE, S>, P) == cudaSuccess ? HS_OK : HS_ECUDA;
-  }
   k_split_gemm<MODE, S><<<grid, NUM_THREADS, smem, st>>>(P);
   return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
 }
