@@ -673,26 +673,8 @@ def run_main(args, w):
     else:
         launches_per_step = 2 + 1 + (1 if N_f else 0) + 2 + 2
 
-    # ---------------- plain FP64 GPU form, same inputs
-    fp64 = None
-    if split and args.fp64_steps > 0:
-        p64 = hs.hs_plan(w.N_A, w.N_L, w.N_G, "fp64", 0, 0, stream)
-        inf64 = []
-        ms64 = timed_loop(p64, args.fp64_steps, 0, inf64, io)
-        hs.hs_destroy(p64)
-        snap["fp64"] = (H[:, cols].cpu().numpy(), S[:, cols].cpu().numpy())
-        fp64 = {"tflops": F * ws * args.fp64_steps / (ms64 / 1e3) / 1e12,
-                "kpts_per_s": ws * args.fp64_steps / (ms64 / 1e3),
-                "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
-                "phase_ms": {k: statistics.mean(i[k] for i in inf64) for k in
-                             ("ms_factor", "ms_atoms", "ms_S", "ms_H", "ms_finalize")},
-                "roofline": {"bound": "alu", "kernel": "k_contract_fp64 (H)",
-                             "achieved": F_H / (statistics.mean(i["ms_H"] for i in inf64) / 1e3)
-                             / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"}}
-        fp64["roofline"]["frac"] = fp64["roofline"]["achieved"] / FP64_PEAK_TFLOPS
-
-    # ---------------- end to end through hs_assemble_host (pinned host buffers), same plan
+    # ---------------- end to end through hs_assemble_host (pinned host buffers), same plan,
+    # right after the device-resident steps (before the minute-long FP64 form heats the GPU)
     e2e = None
     if not args.no_e2e:
         def pin(t):  # pinned host copy with the same (column-major) strides
@@ -721,6 +703,25 @@ def run_main(args, w):
                "call": "hs_assemble_host (pinned host buffers; copies of A, B, T, U in and "
                        "H, S out inside the timed region)"}
         del hA, hB, hU, hT, hH, hS
+    # ---------------- plain FP64 GPU form, same inputs
+    fp64 = None
+    if split and args.fp64_steps > 0:
+        p64 = hs.hs_plan(w.N_A, w.N_L, w.N_G, "fp64", 0, 0, stream)
+        inf64 = []
+        ms64 = timed_loop(p64, args.fp64_steps, 0, inf64, io)
+        hs.hs_destroy(p64)
+        snap["fp64"] = (H[:, cols].cpu().numpy(), S[:, cols].cpu().numpy())
+        fp64 = {"tflops": F * ws * args.fp64_steps / (ms64 / 1e3) / 1e12,
+                "kpts_per_s": ws * args.fp64_steps / (ms64 / 1e3),
+                "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                "phase_ms": {k: statistics.mean(i[k] for i in inf64) for k in
+                             ("ms_factor", "ms_atoms", "ms_S", "ms_H", "ms_finalize")},
+                "roofline": {"bound": "alu", "kernel": "k_contract_fp64 (H)",
+                             "achieved": F_H / (statistics.mean(i["ms_H"] for i in inf64) / 1e3)
+                             / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"}}
+        fp64["roofline"]["frac"] = fp64["roofline"]["achieved"] / FP64_PEAK_TFLOPS
+
     hs.hs_destroy(plan)
     del H, S, io
     torch.cuda.empty_cache()

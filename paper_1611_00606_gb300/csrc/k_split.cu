@@ -1792,13 +1792,16 @@ int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, do
   P.C = S;
   {
     const int stage_bytes = 4 * s * TILE_BYTES;
-    const int depth = tuned_depth(mode, s, N_L, N_G, n_stage, timed, st, [&](int d) {
+    // trials re-run the S contraction: not when the caller already made S (its mirror
+    // may be running on another stream)
+    const bool tune = timed && !skip_S;
+    const int depth = tuned_depth(mode, s, N_L, N_G, n_stage, tune, st, [&](int d) {
       P.n_stage = d;
       return launch_gemm(mode, s, tiles, smem_for(mode, d, stage_bytes), st, P);
     });
     P.n_stage = depth;
     smem = smem_for(mode, depth, stage_bytes);
-    P.band = tuned_band(mode, s, N_L, N_G, timed, st, [&](int b) {
+    P.band = tuned_band(mode, s, N_L, N_G, tune, st, [&](int b) {
       P.band = b;
       return launch_gemm(mode, s, tiles, smem, st, P);
     });
