@@ -37,33 +37,14 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <functional>
-#include <map>
-#include <memory>
-#include <mutex>
-#include <string>
-#include <vector>
+#include <new>
 
-#include "plan.h"
+#include "split_common.h"
+
+using namespace hs_split;
 
 namespace {
 
-constexpr int BM = 128;        // complex rows per tile (MMA M)
-constexpr int BNC = 64;        // complex columns per tile
-constexpr int BN = 2 * BNC;    // MMA N (Re | Im)
-constexpr int KB = 16;         // real K per pipeline stage (= one MMA K step)
-constexpr int WIN = 8;         // stages per exact window (128 real K)
-constexpr int ROWS_ALIGN = 128;
-constexpr int kMaxBatch = 16;                 // requests per grouped per-atom launch
-constexpr int kMaxMaps = 2 + 2 * kMaxBatch;   // >= 13 for a contraction
-constexpr int kMaxJobs = 7;
-constexpr int TILE_BYTES = 64 * KB * 2;  // one 64-row TMA box: 2 KB
-constexpr int NUM_DRAIN_WARPS = 16;     // four per TMEM lane quarter
-constexpr int NUM_THREADS = 64 + 32 * NUM_DRAIN_WARPS;  // warp 0 TMA, warp 1 MMA, then drain
-constexpr uint64_t kWaitNs = 2000000000ull;  // bounded waits: 2 s
-// contraction epilogue staging in the (then idle) stage ring: (hi, lo) float2 as
-// [2 strips x 64 columns][128 rows], plus 128 row and 128 column exponents
-constexpr int STAGING_CONTRACT = 2 * 64 * 128 * 8 + 256 * 4;
 // ------------------------------------------------------------------ PTX helpers
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -303,62 +284,6 @@ __device__ __forceinline__ double pair_scaled(float hi, float lo, int k) {
 // TMEM accumulators and the double-float drain; they differ in where each
 // K segment's tiles come from, which exponents scale the drain, and the
 // epilogue.
-
-// The _R modes are the real-symmetric variant (real A, B, T, U; H, S real symmetric,
-// Sec. 1.1): operands hold one real K position per row, contraction tiles are
-// 128 x 128 real outputs (B rows = 128 columns of R'), operator rows n = L.
-enum { MODE_CONTRACT = 0, MODE_ATOMS = 1, MODE_CONTRACT_R = 2, MODE_ATOMS_R = 3 };
-__host__ __device__ constexpr bool is_contract(int mode) { return (mode & 1) == 0; }
-__host__ __device__ constexpr bool is_real(int mode) { return mode >= 2; }
-
-struct SplitSeg {
-  int mL, mR;       // tensor maps: L' as the left operand, R as the right one
-                    // (complex: its plain and rotated slices, interleaved by plane)
-  int kblocks;      // stages of KB real K
-  const int* eL;    // exponents of the L source columns
-  const int* eR;    // exponents of the R source columns
-};
-
-// One request of a grouped per-atom launch.
-struct AtomsReq {
-  int mA, mB;         // coefficient slice maps (plain) of this request
-  const int* eA;      // column exponents of its A, B slices
-  const int* eB;
-  double2* Z;         // outputs, column-major, leading dimension AtomsArgs::ld
-  double2* W2;
-  int N_G;
-  int ngblk;          // 128-row blocks of G
-  int tile0;          // first CTA index of this request in the grouped grid
-};
-
-struct AtomsArgs {
-  AtomsReq rq[kMaxBatch];
-  int nreq;
-  int mOp[2];             // operator slice maps: [0] Z job, [1] W2 job (shared by requests)
-  const int* eOp[2];      // operator row exponents [a][n_pad]
-  const int* slot;        // W2 slot of each atom
-  int ld;
-  int N_A, N_L, P;        // P: operator K per part (an atom's widest K block range)
-  int n_pad, ntile;
-};
-
-struct SplitParams {
-  CUtensorMap maps[kMaxMaps];
-  SplitSeg seg[kMaxSeg];
-  int nseg;
-  int s;          // slices
-  int n_stage;    // pipeline depth
-  int N_G, ldC, nbj;
-  int nbi, band;   // contraction: 128-row blocks, row blocks per band of the tile order
-  int bi0;         // contraction: first row block of this launch (tiles of rows [bi0, nbi))
-  int ntiles;      // tiles of the launch; a CTA runs tiles blockIdx.x, + gridDim.x, ...
-  int rows_pad;   // slice p of a coefficient-side array starts at row p * rows_pad
-  double2* C;
-  int* err;
-  int stall;  // test only: the producer arms no stage and issues no copy, so the MMA
-              // thread's and the drain's waits run out (failure-path test)
-  AtomsArgs at;
-};
 
 // Where one K segment of this CTA's tile lives (blocked slice arrays:
 // plane = slice p (+ atom * s for operators), 64-row blocks, 16-wide K blocks).
@@ -827,493 +752,29 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
   }
 }
 
-// ------------------------------------------------------------------ slicers
-
-// Layout shared by every coefficient-side slice array.  Along K the source's
-// complex rows are packed: row k sits at real position 2k (+1 for the imaginary
-// part), and the length 2 nblk N_L is padded with zeros to kpad = roundup(., 16).
-// A contraction runs over kpad real K; the per-atom products read atom a's rows
-// [2 a N_L, 2 (a+1) N_L) as whole 16-wide K blocks, the operator slices of atom a
-// being shifted by the same offset (2 a N_L) mod 16 and zero outside the atom.
-// In memory each slice plane is blocked as [64-row block][16-wide K block][64 rows]
-// [16 elements]: one 2 KB tile per (row block, K block), contiguous, which is
-// exactly one TMA box (the TMA applies the 32-byte swizzle on the way to smem).
-__device__ __forceinline__ size_t tile_off(int row, int j, int NKB) {
-  // element offset of the complex pair j (real elements 2j, 2j+1) of a row
-  return ((size_t)((row >> 6) * NKB + (j >> 3)) * 64 + (row & 63)) * 16 + 2 * (j & 7);
-}
-struct SliceJob {
-  const double2* X;  // source: nblk * N_L complex rows x N_G, column-major, ld ldX
-  const double* u;   // optional real row weight (the U norms), may be null
-  uint16_t* plain;   // [s][rows_pad][kpad] BF16 slices of (re, im) pairs, or with rot
-                     // [s][2][rows_pad][kpad]: (re, im) and (im, -re) slices interleaved
-  int rot;           // nonzero: also write the (im, -re) slices
-  int* expo;         // [rows_pad] column exponents
-  int ldX, nblk;
-};
-struct SliceParams {
-  SliceJob job[kMaxJobs];
-  int s, N_G, rows_pad, N_L;
-  int g0;  // first operand column of this launch (block x slices column g0 + x)
-};
-
-// Balanced base-512 digits of round(x * 2^(9(s-1) - E)); d[0] is the leading one.
-__device__ __forceinline__ void digits_of(double x, int E, int s, int (&d)[kMaxSlices]) {
-  const long long bits = __double_as_longlong(x);
-  const int ex = (int)((bits >> 52) & 0x7FF);
-  long long Y = 0;
-  if (ex != 0) {
-    const long long m = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
-    const int sh = ex - 1075 - E + 9 * (s - 1);
-    if (sh >= 0) {
-      Y = m << sh;
-    } else if (sh > -63) {
-      const int n = -sh;
-      Y = (m + (1LL << (n - 1))) >> n;
-    }
-    if (bits < 0) Y = -Y;
-  }
-#pragma unroll
-  for (int p = kMaxSlices - 1; p >= 1; --p) {
-    if (p < s) {
-      const long long dp = ((Y + 256) & 511) - 256;
-      d[p] = (int)dp;
-      Y = (Y - dp) >> 9;
-    }
-  }
-  d[0] = (int)Y;
-}
-
-// BF16 bits of d * sc for a digit |d| <= 256 and sc = 2^-9p: the value has at most 8
-// significant bits, so it is exact in BF16 and its BF16 bits are the upper half of its
-// FP32 bits.  d converts with the 1.5 * 2^23 magic number (FP32 add, exact for
-// |d| < 2^22) instead of an int-to-float conversion: the slicer writes 20 BF16 values
-// per complex entry and the conversion units (a quarter of the FP32 rate) were its
-// limit.
-__device__ __forceinline__ uint32_t bf16_digit(int d, float sc) {
-  const float f = (__int_as_float(0x4B400000 + d) - 12582912.0f) * sc;
-  return __float_as_uint(f) >> 16;
-}
-
-// |x| as its bit pattern (non-negative doubles order like their bit patterns), 0 for a
-// non-finite x: column maxima are taken with integer instructions, off the FP64 pipe
-// (about two instructions per clock per SM on GB300).
-__device__ __forceinline__ unsigned long long finite_abs_bits(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-  return (b >> 52) == 0x7FFull ? 0ull : b;
-}
-__device__ __forceinline__ bool finite_bits(double x) {
-  return ((__double_as_longlong(x) >> 52) & 0x7FF) != 0x7FF;
-}
-
-// Exponent E with max / 2^E in [64, 128) (0 for an all-zero or non-finite max).
-__device__ __forceinline__ int slice_exponent(double mm) {
-  int e = 0;
-  if (mm > 0.0 && isfinite(mm)) {
-    frexp(mm, &e);
-    return e - 7;
-  }
-  return 0;
-}
-
-// Write the s slices of one complex entry (re, im): plain (re, im) at base + p pstride +
-// off and, with rot, rotated (im, -re) at base + rot_off + p pstride + off.
-__device__ __forceinline__ void put_slices(double2 v, bool zero, int E, int s, uint16_t* base,
-                                           bool rot, size_t pstride, size_t rot_off,
-                                           size_t off) {
-  int dr[kMaxSlices], di[kMaxSlices];
-  const bool bad = !zero && !(finite_bits(v.x) && finite_bits(v.y));
-  if (!zero) {
-    digits_of(v.x, E, s, dr);
-    digits_of(v.y, E, s, di);
-  } else {
-#pragma unroll
-    for (int p = 0; p < kMaxSlices; ++p) dr[p] = di[p] = 0;
-  }
-#pragma unroll
-  for (int p = 0; p < kMaxSlices; ++p) {
-    if (p < s) {
-      const float sc = __int_as_float((127 - 9 * p) << 23);  // 2^{-9p}
-      uint32_t pl, rt;
-      if (bad) {
-        pl = rt = 0x7FC07FC0u;  // NaN pair: propagates through the MMA
-      } else {
-        const uint32_t br = bf16_digit(dr[p], sc), bi = bf16_digit(di[p], sc);
-        pl = br | (bi << 16);
-        rt = bi | ((br == 0u ? 0u : br ^ 0x8000u) << 16);  // -dr: sign flip (zero stays +0)
-      }
-      *(uint32_t*)(base + p * pstride + off) = pl;
-      if (rot) *(uint32_t*)(base + rot_off + p * pstride + off) = rt;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(256) k_slice(const __grid_constant__ SliceParams P) {
-  const SliceJob J = P.job[blockIdx.y];
-  const int g = P.g0 + blockIdx.x;
-  const int s = P.s;
-  const int K = J.nblk * P.N_L;                  // complex rows of the source
-  const int kpad = ((2 * K + KB - 1) / KB) * KB;  // packed real K, whole 16-wide blocks
-  const size_t slice_elems = (size_t)P.rows_pad * kpad;
-  const size_t pstride = (J.rot ? 2 : 1) * slice_elems;  // plain slice p at p pstride
-  __shared__ unsigned long long red[32];
-  __shared__ int s_E;
-  const int kc = kpad / 2;  // complex positions per padded row
-  const int NKB = kpad / KB;
-  if (g >= P.N_G) {
-    for (int k = threadIdx.x; k < kc; k += blockDim.x)
-      for (int p = 0; p < s; ++p) {
-        *(uint32_t*)(J.plain + p * pstride + tile_off(g, k, NKB)) = 0u;
-        if (J.rot) *(uint32_t*)(J.plain + slice_elems + p * pstride + tile_off(g, k, NKB)) = 0u;
-      }
-    if (threadIdx.x == 0) J.expo[g] = 0;
-    return;
-  }
-  const double2* col = J.X + (size_t)g * J.ldX;
-  unsigned long long m = 0ull;  // bit pattern of the column's largest finite |component| (x |u|)
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    const double2 v = col[k];
-    unsigned long long a = max(finite_abs_bits(v.x), finite_abs_bits(v.y));
-    if (J.u) a = finite_abs_bits(__longlong_as_double((long long)a) * fabs(J.u[k]));
-    m = max(m, a);
-  }
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long mm = 0ull;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = max(mm, red[i]);
-    s_E = slice_exponent(__longlong_as_double((long long)mm));
-    J.expo[g] = s_E;
-  }
-  __syncthreads();
-  const int E = s_E;
-  for (int j = threadIdx.x; j < kc; j += blockDim.x) {
-    const bool zero = (j >= K);
-    double2 v = make_double2(0.0, 0.0);
-    if (!zero) {
-      v = col[j];
-      if (J.u) {
-        v.x *= J.u[j];
-        v.y *= J.u[j];
-      }
-    }
-    put_slices(v, zero, E, s, J.plain, J.rot != 0, pstride, slice_elems, tile_off(g, j, NKB));
-  }
-}
-
-// Slices of the per-atom operators (k-independent, once per factorisation):
-// job 0: MZ[a] (N_L x 2N_L), K = [A part | B part] = 2P; job 1: M2[a] (N_L x N_L),
-// K = P, P = the widest K block range of an atom in the packed coefficient layout.
-// Column l of a part sits at real position (2 a N_L) mod 16 + 2l, the offset of
-// atom a's rows inside its first K block, zeros elsewhere.  Real row n = 2L + c of
-// output row L: c = 0 gives Re, c = 1 gives Im:
-//   row 2L:   (Re M(L,k), -Im M(L,k)) pairs;   row 2L+1: (Im M(L,k), Re M(L,k)).
-// Layout [a][p][n_pad][Kop]; one exponent per (a, n), shared by rows 2L, 2L+1.
-__global__ void __launch_bounds__(128) k_slice_op(const double2* __restrict__ M, int job, int N_A,
-                                                  int N_L, int P, int n_pad, int s,
-                                                  uint16_t* __restrict__ out,
-                                                  int* __restrict__ expo) {
-  const int a = blockIdx.y, n = blockIdx.x;  // n < n_pad
-  const int parts = job == 0 ? 2 : 1;
-  const int Kop = parts * P;
-  const size_t slice_elems = (size_t)n_pad * Kop;
-  uint16_t* base = out + (size_t)a * s * slice_elems;
-  const int L = n >> 1, c = n & 1;
-  const int ldM = N_L;
-  const double2* Ma = M + (size_t)a * N_L * (parts * N_L);
-  __shared__ double red[4];
-  __shared__ int s_E;
-  double m = 0.0;
-  if (L < N_L)
-    for (int k = threadIdx.x; k < parts * N_L; k += blockDim.x) {
-      const double2 v = Ma[L + (size_t)k * ldM];
-      m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
-    }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const double mm = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
-    s_E = slice_exponent(mm);
-    expo[(size_t)a * n_pad + n] = s_E;
-  }
-  __syncthreads();
-  const int E = s_E;
-  const int hp = P / 2;
-  const int oc = ((2 * a * N_L) & (KB - 1)) >> 1;  // complex offset of atom a in its K block
-  for (int j = threadIdx.x; j < Kop / 2; j += blockDim.x) {
-    const int part = j / hp, l = j - part * hp - oc;
-    const bool zero = (L >= N_L) || (l < 0) || (l >= N_L);
-    double2 v = make_double2(0.0, 0.0);
-    if (!zero) {
-      const double2 mv = Ma[L + (size_t)(part * N_L + l) * ldM];
-      v = c == 0 ? make_double2(mv.x, -mv.y) : make_double2(mv.y, mv.x);
-    }
-    put_slices(v, zero, E, s, base, false, slice_elems, 0, tile_off(n, j, Kop / KB));
-  }
-}
-
-// Real sources (real-symmetric variant): nblk * N_L real rows per column, packed one
-// K position per row (kpad = roundup(K, 16)); a thread writes the pair of positions
-// (2j, 2j + 1) as one 32-bit word per slice, with k_slice's digit and exponent rules
-// (no rotated copy: a real contraction needs none).
-__global__ void __launch_bounds__(256) k_slice_real(const __grid_constant__ SliceParams P) {
-  const SliceJob J = P.job[blockIdx.y];
-  const int g = P.g0 + blockIdx.x;
-  const int s = P.s;
-  const int K = J.nblk * P.N_L;                // real rows of the source
-  const int kpad = ((K + KB - 1) / KB) * KB;   // packed K, whole 16-wide blocks
-  const size_t slice_elems = (size_t)P.rows_pad * kpad;
-  __shared__ unsigned long long red[32];
-  __shared__ int s_E;
-  const int kc = kpad / 2;  // position pairs per row
-  const int NKB = kpad / KB;
-  if (g >= P.N_G) {
-    for (int k = threadIdx.x; k < kc; k += blockDim.x)
-      for (int p = 0; p < s; ++p)
-        *(uint32_t*)(J.plain + p * slice_elems + tile_off(g, k, NKB)) = 0u;
-    if (threadIdx.x == 0) J.expo[g] = 0;
-    return;
-  }
-  const double* col = (const double*)J.X + (size_t)g * J.ldX;
-  unsigned long long m = 0ull;  // bit pattern of the column's largest finite |value| (x |u|)
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    const double v = col[k];
-    m = max(m, finite_abs_bits(J.u ? v * J.u[k] : v));
-  }
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long mm = 0ull;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mm = max(mm, red[i]);
-    s_E = slice_exponent(__longlong_as_double((long long)mm));
-    J.expo[g] = s_E;
-  }
-  __syncthreads();
-  const int E = s_E;
-  for (int j = threadIdx.x; j < kc; j += blockDim.x) {
-    const int k0 = 2 * j, k1 = k0 + 1;
-    double x0 = k0 < K ? col[k0] : 0.0, x1 = k1 < K ? col[k1] : 0.0;
-    if (J.u) {
-      if (k0 < K) x0 *= J.u[k0];
-      if (k1 < K) x1 *= J.u[k1];
-    }
-    put_slices(make_double2(x0, x1), k0 >= K, E, s, J.plain, false, slice_elems, 0,
-               tile_off(g, j, NKB));
-  }
-}
-
-// Real per-atom operators: the real parts of the (embedded) MZ[a] and M2[a]; operator
-// row n = output row L; column l of a part at real position (a N_L) mod 16 + l of the
-// part, zeros elsewhere (the packed real layout's offset of atom a).
-__global__ void __launch_bounds__(128) k_slice_op_real(const double2* __restrict__ M, int job,
-                                                       int N_A, int N_L, int P, int n_pad, int s,
-                                                       uint16_t* __restrict__ out,
-                                                       int* __restrict__ expo) {
-  const int a = blockIdx.y, L = blockIdx.x;  // L < n_pad
-  const int parts = job == 0 ? 2 : 1;
-  const int Kop = parts * P;
-  const size_t slice_elems = (size_t)n_pad * Kop;
-  uint16_t* base = out + (size_t)a * s * slice_elems;
-  const int ldM = N_L;
-  const double2* Ma = M + (size_t)a * N_L * (parts * N_L);
-  __shared__ unsigned long long red[4];
-  __shared__ int s_E;
-  unsigned long long m = 0ull;
-  if (L < N_L)
-    for (int k = threadIdx.x; k < parts * N_L; k += blockDim.x)
-      m = max(m, finite_abs_bits(Ma[L + (size_t)k * ldM].x));
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned long long mm = max(max(red[0], red[1]), max(red[2], red[3]));
-    s_E = slice_exponent(__longlong_as_double((long long)mm));
-    expo[(size_t)a * n_pad + L] = s_E;
-  }
-  __syncthreads();
-  const int E = s_E;
-  const int oa = (a * N_L) & (KB - 1);  // atom a's offset inside its first K block
-  for (int j = threadIdx.x; j < Kop / 2; j += blockDim.x) {
-    double x[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int q = 2 * j + h;
-      const int part = q / P, l = q - part * P - oa;
-      x[h] = (L < N_L && l >= 0 && l < N_L) ? Ma[L + (size_t)(part * N_L + l) * ldM].x : 0.0;
-    }
-    put_slices(make_double2(x[0], x[1]), L >= N_L, E, s, base, false, slice_elems, 0,
-               tile_off(L, j, Kop / KB));
-  }
-}
-
-// ------------------------------------------------------------------ host side
-
-PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      return (PFN_cuTensorMapEncodeTiled_v12000)p;
-    cudaGetLastError();
-    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
-  }();
-  return fn;
-}
-
-// Tensor map over a blocked slice array: dims (16 elements, 64 rows, NKB K blocks,
-// NRB row blocks, planes `plane_tiles` tiles of 2 KB apart), box (16, 64, 1, box_rb,
-// box_planes): every (row block, plane) of a box is one contiguous 2 KB tile, so a box
-// lands in shared memory as [plane][row block] 2 KB tiles.
-bool encode_tiles(CUtensorMap* m, const uint16_t* base, int NKB, int NRB, int planes,
-                  size_t plane_tiles, int box_rb, int box_planes) {
-  auto fn = get_encode();
-  if (!fn) return false;
-  if (box_rb < 1 || box_rb > NRB || box_planes < 1 || box_planes > planes) return false;
-  cuuint64_t dims[5] = {(cuuint64_t)KB, 64u, (cuuint64_t)NKB, (cuuint64_t)NRB, (cuuint64_t)planes};
-  cuuint64_t strides[4] = {(cuuint64_t)KB * 2, (cuuint64_t)TILE_BYTES,
-                           (cuuint64_t)NKB * TILE_BYTES, (cuuint64_t)plane_tiles * TILE_BYTES};
-  cuuint32_t box[5] = {(cuuint32_t)KB, 64u, 1u, (cuuint32_t)box_rb, (cuuint32_t)box_planes};
-  cuuint32_t estr[5] = {1u, 1u, 1u, 1u, 1u};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)base, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
-// Maps over the slices of one operand source with NKB K blocks and NRB 64-row blocks.
-// A source with a rotated copy stores plain and rotated slices interleaved by plane
-// (plane 2p: slice p of (re, im) pairs, plane 2p + 1: slice p of (im, -re) pairs).
-//  * left role: the s plain slices of two row blocks (128 rows) per box;
-//  * right role, complex: the plain and rotated slices of one row block (64 columns)
-//    per box (2 s planes); right role, real: as the left role (128 columns).
-bool encode_left(CUtensorMap* m, const uint16_t* base, int NKB, int NRB, int s, bool rot) {
-  const size_t plane = (size_t)NRB * NKB * (rot ? 2 : 1);
-  return encode_tiles(m, base, NKB, NRB, s, plane, 2, s);
-}
-bool encode_right(CUtensorMap* m, const uint16_t* base, int NKB, int NRB, int s, bool rot) {
-  if (!rot) return encode_left(m, base, NKB, NRB, s, false);
-  return encode_tiles(m, base, NKB, NRB, 2 * s, (size_t)NRB * NKB, 1, 2 * s);
-}
-
 }  // namespace
 
-// Rows (operand columns g) of a slice array: whole 128-row blocks; 256 for real plans,
-// whose contraction column pairs span 256 columns.
-static inline int rows_pad_of(int N_G, bool real = false) {
-  const int al = real ? 2 * ROWS_ALIGN : ROWS_ALIGN;
-  return ((N_G + al - 1) / al) * al;
-}
-// Packed real K of a source of nblk blocks of N_L rows (whole 16-wide blocks): two
-// positions per complex row, one per real row.
-static inline int kpad_of(int nblk, int N_L, bool real = false) {
-  return (((real ? 1 : 2) * nblk * N_L + KB - 1) / KB) * KB;
-}
-// Real K of one part of a per-atom operator: the most 16-wide K blocks any atom's
-// rows [pr a N_L, pr (a+1) N_L) of the packed layout touch (pr positions per row).
-static int op_part_k(int N_A, int N_L, bool real = false) {
-  const int pr = real ? 1 : 2;
-  int nkb = 0;
-  for (int a = 0; a < N_A; ++a)
-    nkb = std::max(nkb, (pr * (a + 1) * N_L + KB - 1) / KB - (pr * a * N_L) / KB);
-  return nkb * KB;
-}
-// Operator rows (2 N_L real rows; N_L for real plans) padded to whole 128-row tiles.
-static inline int op_rows_pad(int N_L, bool real = false) {
-  return (((real ? 1 : 2) * N_L + BN - 1) / BN) * BN;
+// ------------------------------------------------------------------ launches
+
+// The grouped per-atom launch as the single kernel node of a CUDA graph:
+// captured once per plan, then re-parameterised (cudaGraphExecKernelNodeSetParams:
+// grid and arguments of this batch) and replayed for every batch.  Updates only
+// affect later launches, so a replay still running is undisturbed.
+struct AtomsGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t node = nullptr;
+};
+
+AtomsGraph* hs_atoms_graph_new() { return new (std::nothrow) AtomsGraph(); }
+void hs_atoms_graph_free(AtomsGraph* a) {
+  if (!a) return;
+  if (a->exec) cudaGraphExecDestroy(a->exec);
+  if (a->g) cudaGraphDestroy(a->g);
+  delete a;
 }
 
-// Blocks (of N_L complex rows) of each source and whether it needs the rotated copy.
-static void source_shape(int src, int N_A, int n_fail, bool real, int& nblk, bool& rot) {
-  rot = !real && (src != SRC_AF);
-  nblk = (src == SRC_AF || src == SRC_X) ? n_fail : N_A;
-}
-
-size_t hs_plan_s::split_ws_bytes(int N_G, int n_fail) const {
-  if (precision != HS_SPLIT_BF16) return 0;
-  const int nf = n_fail > 0 ? n_fail : 1;
-  const int rp = rows_pad_of(N_G, real);
-  size_t b = 0;
-  for (int src = 0; src < NSRC; ++src) {
-    int nblk;
-    bool rot;
-    source_shape(src, N_A, nf, real, nblk, rot);
-    const size_t one = (size_t)slices * rp * kpad_of(nblk, N_L, real) * 2;
-    b += (rot ? 2 : 1) * one + sizeof(int) * rp;
-  }
-  return b;
-}
-
-int hs_plan_s::split_ws_alloc(Workspace& w, int N_G, int n_fail, cudaStream_t st, bool async) {
-  if (precision != HS_SPLIT_BF16) return HS_OK;
-  if (!get_encode()) return HS_ECUDA;
-  const int rp = rows_pad_of(N_G, real);
-  auto al = [&](void** ptr, size_t bytes) -> bool {
-    return (async ? hs_malloc_async(ptr, bytes, st, hs_serve_pool(this)) : cudaMalloc(ptr, bytes)) ==
-           cudaSuccess;
-  };
-  for (int src = 0; src < NSRC; ++src) {
-    int nblk;
-    bool rot;
-    source_shape(src, N_A, n_fail, real, nblk, rot);
-    const size_t one = (size_t)slices * rp * kpad_of(nblk, N_L, real) * 2;
-    if (!al((void**)&w.sb[src].plain, (rot ? 2 : 1) * one)) return HS_ENOMEM;
-    w.sb[src].rot = rot;
-    if (!al((void**)&w.sb[src].expo, sizeof(int) * rp)) return HS_ENOMEM;
-  }
-  return HS_OK;
-}
-
-size_t hs_plan_s::split_fixed_bytes() const {
-  if (precision != HS_SPLIT_BF16) return 0;
-  const size_t P = (size_t)op_part_k(N_A, N_L, real), np = (size_t)op_rows_pad(N_L, real);
-  return (size_t)N_A * slices * np * (3 * P) * 2 + 2 * sizeof(int) * N_A * np;
-}
-
-int hs_plan_s::split_plan_alloc() {
-  if (precision != HS_SPLIT_BF16) return HS_OK;
-  if (!get_encode()) return HS_ECUDA;
-  const size_t P = (size_t)op_part_k(N_A, N_L, real), np = (size_t)op_rows_pad(N_L, real);
-  const size_t zb = (size_t)N_A * slices * np * 2 * P * 2, wb = zb / 2;
-  if (cudaMalloc((void**)&op_slices[0], zb) != cudaSuccess ||
-      cudaMalloc((void**)&op_slices[1], wb) != cudaSuccess ||
-      cudaMalloc((void**)&op_expo[0], sizeof(int) * N_A * np) != cudaSuccess ||
-      cudaMalloc((void**)&op_expo[1], sizeof(int) * N_A * np) != cudaSuccess) {
-    cudaGetLastError();
-    return HS_ENOMEM;
-  }
-  return HS_OK;
-}
-
-void hs_plan_s::split_plan_release() {
-  for (int j = 0; j < 2; ++j) {
-    if (op_slices[j]) cudaFree(op_slices[j]);
-    if (op_expo[j]) cudaFree(op_expo[j]);
-    op_slices[j] = nullptr;
-    op_expo[j] = nullptr;
-  }
-}
-
-// Slice MZ and M2 (k-independent) after every factorisation.
-int hs_plan_s::split_factor(cudaStream_t st) {
-  if (precision != HS_SPLIT_BF16) return HS_OK;
-  const int P = op_part_k(N_A, N_L, real), np = op_rows_pad(N_L, real);
-  for (int job = 0; job < 2; ++job) {
-    const double2* M = job == 0 ? MZ : M2;
-    if (real)
-      k_slice_op_real<<<dim3(np, N_A), 128, 0, st>>>(M, job, N_A, N_L, P, np, slices,
-                                                      op_slices[job], op_expo[job]);
-    else
-      k_slice_op<<<dim3(np, N_A), 128, 0, st>>>(M, job, N_A, N_L, P, np, slices, op_slices[job],
-                                                 op_expo[job]);
-    HS_CUDA_TRY(cudaGetLastError());
-  }
-  return HS_OK;
-}
+namespace hs_split {
 
 static int set_smem(const void* fn, size_t smem) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
@@ -1343,19 +804,11 @@ static int launch_mode(int s, int grid, size_t smem, cudaStream_t st, const Spli
   }
 }
 
-// Test-only stall injection (HS_TEST_STALL=1): every slice-GEMM launch arms no stage and
-// issues no copy, so its bounded waits give up (2 s) and the kernel sets the device error
-// word and returns (the host sees HS_EDEVICE).  Read at every launch.
-static bool stall_injection() {
-  const char* e = std::getenv("HS_TEST_STALL");
-  return e && e[0] == '1';
-}
-
 // The launch parameters as they go to the device: the stall flag.
 static void set_waits(SplitParams& P) { P.stall = stall_injection() ? 1 : 0; }
 
-static int launch_gemm(int mode, int s, int grid, size_t smem, cudaStream_t st,
-                       const SplitParams& P0) {
+int launch_gemm(int mode, int s, int grid, size_t smem, cudaStream_t st,
+                const SplitParams& P0) {
   SplitParams P = P0;
   set_waits(P);
   switch (mode) {
@@ -1381,26 +834,8 @@ static const void* atoms_fn_m(int s) {
 }
 static const void* atoms_fn(int s) { return atoms_fn_m<MODE_ATOMS>(s); }
 
-// The grouped per-atom launch as the single kernel node of a CUDA graph:
-// captured once per plan, then re-parameterised (cudaGraphExecKernelNodeSetParams:
-// grid and arguments of this batch) and replayed for every batch.  Updates only
-// affect later launches, so a replay still running is undisturbed.
-struct AtomsGraph {
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t node = nullptr;
-};
-
-AtomsGraph* hs_atoms_graph_new() { return new (std::nothrow) AtomsGraph(); }
-void hs_atoms_graph_free(AtomsGraph* a) {
-  if (!a) return;
-  if (a->exec) cudaGraphExecDestroy(a->exec);
-  if (a->g) cudaGraphDestroy(a->g);
-  delete a;
-}
-
-static int graph_launch_atoms(AtomsGraph& G, int s, int grid, size_t smem, cudaStream_t st,
-                              const SplitParams& P0) {
+int graph_launch_atoms(AtomsGraph& G, int s, int grid, size_t smem, cudaStream_t st,
+                       const SplitParams& P0) {
   SplitParams P = P0;
   set_waits(P);
   const void* fn = atoms_fn(s);
@@ -1426,784 +861,5 @@ static int graph_launch_atoms(AtomsGraph& G, int s, int grid, size_t smem, cudaS
   return HS_OK;
 }
 
-// ---------------------------------------------------------------- autotuner
-// Launch knobs tuned on the real work: the first synchronous assembly with an untuned
-// key times every candidate value (the trial launches compute the same result as the
-// final one) and keeps the fastest; a candidate other than the first must win by 2 %.
-//  * ring depth (TMA pipeline stages) of each kernel mode, key "mode:s:N_L:bucket";
-//  * the contraction's band width (row blocks per band of its tile order, which sets
-//    how compact the block of tiles resident at one time is and so the L2 reuse of
-//    the slice boxes), key "band:mode:s:N_L:bucket", candidates 8, 4, 16, 32;
-//  * the slicer's block size (threads per operand column), key
-//    "slice:real:s:N_L:bucket", candidates 256, 128.
-// bucket = N_G / 1024 rounded up.  Serving requests use tuned values when there are
-// some and the defaults otherwise.  HS_AUTOTUNE=0 disables tuning; HS_TUNE_CACHE=<file>
-// loads (whenever the name changes) and appends "key value" lines.  The per-atom kernel's grid is not a knob: its
-// ring fills an SM's shared memory, so it runs one CTA per SM by construction.
-namespace {
-std::mutex g_tune_mu;
-std::map<std::string, int> g_tune;
-std::string g_tune_path;  // the HS_TUNE_CACHE file read last ("" = none yet)
 
-std::string tune_key(int mode, int s, int N_L, int N_G) {
-  return std::to_string(mode) + ":" + std::to_string(s) + ":" + std::to_string(N_L) + ":" +
-         std::to_string((N_G + 1023) / 1024);
-}
-
-// Reads the cache file named by HS_TUNE_CACHE whenever that name changes (its values
-// override the ones in memory).
-void tune_load_locked() {
-  const char* path = std::getenv("HS_TUNE_CACHE");
-  if (!path || g_tune_path == path) return;
-  g_tune_path = path;
-  std::FILE* f = std::fopen(path, "r");
-  if (!f) return;
-  char key[128];
-  int v;
-  while (std::fscanf(f, "%127s %d", key, &v) == 2) g_tune[key] = v;
-  std::fclose(f);
-}
-
-void tune_store_locked(const std::string& key, int v) {
-  g_tune[key] = v;
-  const char* path = std::getenv("HS_TUNE_CACHE");
-  if (!path) return;
-  std::FILE* f = std::fopen(path, "a");
-  if (!f) return;
-  std::fprintf(f, "%s %d\n", key.c_str(), v);
-  std::fclose(f);
-}
-
-size_t smem_for(int mode, int n_stage, int stage_bytes) {
-  const size_t ring = (size_t)n_stage * stage_bytes;
-  return (is_contract(mode) ? std::max(ring, (size_t)STAGING_CONTRACT) : ring) + 1024 + 256;
-}
-
-// The cached value of `key` if any; else, when tuning is allowed, the fastest of
-// `cand` (cand[0] is the default) timed with `trial(value)`, which enqueues the real
-// work; else cand[0].  `found` tells whether the value came from the cache.
-int tuned_choice(const std::string& key, const std::vector<int>& cand, bool allow,
-                 cudaStream_t st, const std::function<int(int)>& trial, bool* found = nullptr) {
-  if (found) *found = false;
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    tune_load_locked();
-    auto it = g_tune.find(key);
-    if (it != g_tune.end()) {
-      if (found) *found = true;
-      return it->second;
-    }
-  }
-  const char* env = std::getenv("HS_AUTOTUNE");
-  if (!allow || cand.size() < 2 || (env && env[0] == '0') || stall_injection()) return cand[0];
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess) return cand[0];
-  if (cudaEventCreate(&e1) != cudaSuccess) {
-    cudaEventDestroy(e0);
-    return cand[0];
-  }
-  int best = cand[0];
-  float best_ms = 1e30f;
-  for (int v : cand) {
-    float ms = 0.f;
-    if (cudaEventRecord(e0, st) != cudaSuccess || trial(v) != HS_OK ||
-        cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-      cudaGetLastError();
-      break;
-    }
-    if (ms < 0.98f * best_ms) {  // a later candidate must win clearly
-      best_ms = ms;
-      best = v;
-    }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  tune_store_locked(key, best);
-  return best;
-}
-
-// Depth for this launch; `trial(depth)` enqueues the real work with that depth.
-int tuned_depth(int mode, int s, int N_L, int N_G, int max_depth, bool allow, cudaStream_t st,
-                const std::function<int(int)>& trial) {
-  std::vector<int> cand;
-  for (int d = max_depth; d >= 2; --d) cand.push_back(d);
-  const int v = tuned_choice(tune_key(mode, s, N_L, N_G), cand, allow, st, trial);
-  return std::min(std::max(v, 2), max_depth);
-}
-}  // namespace
-
-// Row blocks per band of the contraction's tile order: tuned per key (8 by default:
-// 152 resident CTAs then span about 8 row blocks x 19 column blocks); HS_BAND > 0 fixes it.
-static int band_override() {
-  static const int band = []() {
-    const char* e = std::getenv("HS_BAND");
-    const int v = e ? std::atoi(e) : 0;
-    return v >= 1 ? v : 0;
-  }();
-  return band;
-}
-static int contract_band(int mode = 0, int s = 0, int N_L = 0, int N_G = 0) {
-  if (band_override()) return band_override();
-  if (s == 0) return 8;
-  bool found = false;
-  const int v = tuned_choice("band:" + tune_key(mode, s, N_L, N_G), {8}, false, nullptr,
-                             [](int) { return HS_OK; }, &found);
-  return found && v >= 1 ? v : 8;
-}
-static int tuned_band(int mode, int s, int N_L, int N_G, bool allow, cudaStream_t st,
-                      const std::function<int(int)>& trial) {
-  if (band_override()) return band_override();
-  const int v = tuned_choice("band:" + tune_key(mode, s, N_L, N_G), {8, 4, 16, 32}, allow, st,
-                             trial);
-  return v >= 1 ? v : 8;
-}
-
-// Threads per slicer block (one block per operand column).
-static int slice_threads(bool real, int s, int N_L, int N_G, bool allow, cudaStream_t st,
-                         const std::function<int(int)>& trial) {
-  const int v = tuned_choice("slice:" + std::to_string(real ? 1 : 0) + ":" + std::to_string(s) +
-                                 ":" + std::to_string(N_L) + ":" +
-                                 std::to_string((N_G + 1023) / 1024),
-                             {256, 128}, allow, st, trial);
-  return v == 128 ? v : 256;
-}
-
-int hs_plan_s::split_geometry(int& n_stage, size_t& smem) const {
-  const int stage_bytes = 4 * slices * TILE_BYTES;
-  const int budget = 227 * 1024 - 1024 - 256;
-  n_stage = budget / stage_bytes;
-  if (n_stage > 8) n_stage = 8;
-  if (n_stage < 2) return HS_EINVAL;
-  smem = smem_for(MODE_CONTRACT, n_stage, stage_bytes);
-  return HS_OK;
-}
-
-static void slice_job(SliceParams& sp, int& nj, Workspace& w, int src, const double2* X, int ldX,
-                      int nblk, const double* u) {
-  SliceBuf& b = w.sb[src];
-  sp.job[nj++] = SliceJob{X, u, b.plain, b.rot, b.expo, ldX, nblk};
-}
-
-static int slice_launch(SliceParams& sp, int nj, int s, int N_G, int rp, int N_L, bool real,
-                        cudaStream_t st, int g0 = 0, int ng = -1, int threads = 256) {
-  if (ng < 0) ng = rp - g0;
-  if (g0 < 0 || ng < 0 || g0 + ng > rp) return HS_EINVAL;
-  if (ng == 0) return HS_OK;  // nothing left to slice
-  if (threads != 128 && threads != 256) return HS_EINVAL;
-  sp.g0 = g0;
-  sp.s = s;
-  sp.N_G = N_G;
-  sp.rows_pad = rp;
-  sp.N_L = N_L;
-  if (real) k_slice_real<<<dim3(ng, nj), threads, 0, st>>>(sp);
-  else k_slice<<<dim3(ng, nj), threads, 0, st>>>(sp);
-  return cudaGetLastError() == cudaSuccess ? HS_OK : HS_ECUDA;
-}
-
-// 1. slice the inputs A, U.B, B of one k-point (tune: time the slicer's block sizes on
-//    this work if its key is untuned)
-int hs_plan_s::split_inputs(const double2* A, const double2* B, int ldAB, const double* U,
-                            int N_G, Workspace& w, cudaStream_t st, int g0, int ng, bool tune) {
-  const int rp = rows_pad_of(N_G, real);
-  if (rows_pad_of(w.N_G, real) < rp || w.n_fail < N_f || !w.sb[SRC_A].plain) return HS_EINVAL;
-  SliceParams sp{};
-  int nj = 0;
-  slice_job(sp, nj, w, SRC_A, A, ldAB, N_A, nullptr);
-  slice_job(sp, nj, w, SRC_UB, B, ldAB, N_A, U);
-  slice_job(sp, nj, w, SRC_B, B, ldAB, N_A, nullptr);
-  const int threads = slice_threads(real, slices, N_L, N_G, tune && g0 == 0 && ng < 0, st,
-                                    [&](int t) {
-                                      return slice_launch(sp, nj, slices, N_G, rp, N_L, real, st,
-                                                          g0, ng, t);
-                                    });
-  return slice_launch(sp, nj, slices, N_G, rp, N_L, real, st, g0, ng, threads);
-}
-
-// 2. per-atom products of up to kMaxBatch k-points in one grouped launch: Z and
-//    W2 = [Y; X] in FP64.  With `graph`, the launch is the (re-parameterised) kernel
-//    node of the plan's captured graph.
-int hs_plan_s::split_atoms(const AtomsJob* jobs, int n, cudaStream_t st, AtomsGraph* graph) {
-  if (n < 1 || n > kMaxBatch) return HS_EINVAL;
-  const int s = slices, Pp = op_part_k(N_A, N_L, real), np = op_rows_pad(N_L, real);
-  const int mode = real ? MODE_ATOMS_R : MODE_ATOMS;
-  int n_stage;
-  size_t smem;
-  int rc = split_geometry(n_stage, smem);
-  if (rc) return rc;
-  SplitParams* PA = new (std::nothrow) SplitParams;
-  if (!PA) return HS_ENOMEM;
-  std::memset(PA, 0, sizeof(*PA));
-  AtomsArgs& at = PA->at;
-  // operator slices [a][p][n_pad][Kop]: the right operand, two row blocks x s planes
-  bool ok = encode_tiles(&PA->maps[0], op_slices[0], 2 * Pp / KB, np / 64, N_A * s,
-                         (size_t)(np / 64) * (2 * Pp / KB), 2, s) &&
-            encode_tiles(&PA->maps[1], op_slices[1], Pp / KB, np / 64, N_A * s,
-                         (size_t)(np / 64) * (Pp / KB), 2, s);
-  at.mOp[0] = 0;
-  at.mOp[1] = 1;
-  int grid = 0;
-  for (int r = 0; r < n && ok; ++r) {
-    Workspace& w = *jobs[r].w;
-    const int rp = rows_pad_of(jobs[r].N_G, real);
-    AtomsReq& R = at.rq[r];
-    R.mA = 2 + 2 * r;
-    R.mB = 3 + 2 * r;
-    const int nkb = kpad_of(N_A, N_L, real) / KB;
-    ok = encode_left(&PA->maps[R.mA], w.sb[SRC_A].plain, nkb, rp / 64, s, w.sb[SRC_A].rot) &&
-         encode_left(&PA->maps[R.mB], w.sb[SRC_B].plain, nkb, rp / 64, s, w.sb[SRC_B].rot);
-    R.eA = w.sb[SRC_A].expo;
-    R.eB = w.sb[SRC_B].expo;
-    R.Z = w.Z;
-    R.W2 = w.W2;
-    R.N_G = jobs[r].N_G;
-    R.ngblk = rp / BM;
-    R.tile0 = grid;
-    grid += R.ngblk * (np / BN) * 2 * N_A;
-  }
-  if (!ok) {
-    delete PA;
-    return HS_ECUDA;
-  }
-  at.nreq = n;
-  // persistent: one CTA per SM, each running every gridDim.x-th tile
-  PA->ntiles = grid;
-  {
-    int dev = 0, nsm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
-      delete PA;
-      return HS_ECUDA;
-    }
-    grid = std::min(grid, nsm);
-  }
-  at.eOp[0] = op_expo[0];
-  at.eOp[1] = op_expo[1];
-  at.slot = slot_d;
-  at.ld = N_A * N_L;
-  at.N_A = N_A;
-  at.N_L = N_L;
-  at.P = Pp;
-  at.n_pad = np;
-  at.ntile = np / BN;
-  PA->s = s;
-  PA->err = err_d;
-  const int stage_bytes = 4 * s * TILE_BYTES;
-  const int depth = tuned_depth(mode, s, N_L, jobs[0].N_G, n_stage, graph == nullptr, st,
-                                [&](int d) {
-                                  PA->n_stage = d;
-                                  return launch_gemm(mode, s, grid, smem_for(mode, d, stage_bytes),
-                                                     st, *PA);
-                                });
-  PA->n_stage = depth;
-  smem = smem_for(mode, depth, stage_bytes);
-  rc = graph ? graph_launch_atoms(*graph, s, grid, smem, st, *PA)
-             : launch_gemm(mode, s, grid, smem, st, *PA);
-  delete PA;
-  return rc;
-}
-
-// 3. gather A_f, slice the per-atom outputs, and the two stacked contractions
-int hs_plan_s::split_outputs(const double2* A, int ldAB, int N_G, double2* H, double2* S,
-                             Workspace& w, cudaStream_t st, bool timed, cudaEvent_t s_done,
-                             bool skip_S, bool mirror) {
-  const int K = N_A * N_L;
-  const int N_h = N_A - N_f;
-  const int s = slices;
-  const int rp = rows_pad_of(N_G, real);
-  const int mode = real ? MODE_CONTRACT_R : MODE_CONTRACT;
-  int n_stage;
-  size_t smem;
-  int rc = split_geometry(n_stage, smem);
-  if (rc) return rc;
-  if (real)
-    HS_CUDA_TRY(hs_launch_gather_af_real((const double*)A, ldAB, fail_list_d, N_f, N_L, N_G,
-                                         (double*)w.AF, st));
-  else
-    HS_CUDA_TRY(hs_launch_gather_af(A, ldAB, fail_list_d, N_f, N_L, N_G, w.AF, st));
-  if (timed) HS_CUDA_TRY(cudaEventRecord(ev[4], st));
-  {
-    SliceParams sp{};
-    int nj = 0;
-    slice_job(sp, nj, w, SRC_Z, w.Z, K, N_A, nullptr);
-    if (N_h > 0) slice_job(sp, nj, w, SRC_Y, w.W2, K, N_h, nullptr);
-    if (N_f > 0) {
-      slice_job(sp, nj, w, SRC_AF, w.AF, N_f * N_L, N_f, nullptr);
-      const double2* X = real ? (const double2*)((const double*)w.W2 + (size_t)N_h * N_L)
-                              : w.W2 + (size_t)N_h * N_L;
-      slice_job(sp, nj, w, SRC_X, X, K, N_f, nullptr);
-    }
-    const int threads = slice_threads(real, s, N_L, N_G, false, st, [](int) { return HS_OK; });
-    rc = slice_launch(sp, nj, s, N_G, rp, N_L, real, st, 0, -1, threads);
-    if (rc) return rc;
-  }
-  if (timed) HS_CUDA_TRY(cudaEventRecord(ev[5], st));
-
-  SplitParams* PP = new (std::nothrow) SplitParams;
-  if (!PP) return HS_ENOMEM;
-  SplitParams& P = *PP;
-  std::memset(&P, 0, sizeof(P));
-  int map_of[NSRC][2];
-  int nm = 0;
-  auto add_map = [&](int src, int nblk) -> bool {  // [0]: left role, [1]: right role
-    SliceBuf& b = w.sb[src];
-    const int nkb = kpad_of(nblk, N_L, real) / KB;
-    map_of[src][0] = nm;
-    if (!encode_left(&P.maps[nm++], b.plain, nkb, rp / 64, s, b.rot)) return false;
-    map_of[src][1] = nm;
-    return encode_right(&P.maps[nm++], b.plain, nkb, rp / 64, s, b.rot);
-  };
-  bool ok = add_map(SRC_A, N_A) && add_map(SRC_UB, N_A) && add_map(SRC_Z, N_A) &&
-            add_map(SRC_B, N_A);
-  if (N_h > 0) ok = ok && add_map(SRC_Y, N_h);
-  if (N_f > 0) ok = ok && add_map(SRC_AF, N_f) && add_map(SRC_X, N_f);
-  if (!ok) {
-    delete PP;
-    return HS_ECUDA;
-  }
-  P.s = s;
-  P.n_stage = n_stage;
-  P.N_G = N_G;
-  P.ldC = N_G;
-  P.nbj = (N_G + (real ? BN : BNC) - 1) / (real ? BN : BNC);  // output column tiles
-  P.rows_pad = rp;
-  P.err = err_d;
-  const int nbi = (N_G + BM - 1) / BM;
-  int tiles = 0;
-  for (int b = 0; b < nbi; ++b)  // CTA pairs: column pair c from row block c (2c if real)
-    tiles += 2 * std::min((real ? b / 2 : b) + 1, (P.nbj + 1) / 2);
-  P.nbi = nbi;
-  P.band = contract_band(mode, s, N_L, N_G);
-  P.ntiles = tiles;  // one tile per CTA
-  auto seg = [&](int srcL, int srcR, int nblk) {
-    SplitSeg g;
-    g.mL = map_of[srcL][0];
-    g.mR = map_of[srcR][1];
-    g.kblocks = kpad_of(nblk, N_L, real) / KB;
-    g.eL = w.sb[srcL].expo;
-    g.eR = w.sb[srcR].expo;
-    return g;
-  };
-  // S = A^H A + (UB)^H (UB)
-  P.nseg = 2;
-  P.seg[0] = seg(SRC_A, SRC_A, N_A);
-  P.seg[1] = seg(SRC_UB, SRC_UB, N_A);
-  P.C = S;
-  {
-    const int stage_bytes = 4 * s * TILE_BYTES;
-    // trials re-run the S contraction: not when the caller already made S (its mirror
-    // may be running on another stream)
-    const bool tune = timed && !skip_S;
-    const int depth = tuned_depth(mode, s, N_L, N_G, n_stage, tune, st, [&](int d) {
-      P.n_stage = d;
-      return launch_gemm(mode, s, tiles, smem_for(mode, d, stage_bytes), st, P);
-    });
-    P.n_stage = depth;
-    smem = smem_for(mode, depth, stage_bytes);
-    P.band = tuned_band(mode, s, N_L, N_G, tune, st, [&](int b) {
-      P.band = b;
-      return launch_gemm(mode, s, tiles, smem, st, P);
-    });
-  }
-  if (!skip_S) rc = launch_gemm(mode, s, tiles, smem, st, P);
-  if (rc == HS_OK && !skip_S && mirror) {  // S is final once mirrored: it can leave while H runs
-    const cudaError_t e = real ? hs_launch_mirror_real((double*)S, N_G, N_G, st)
-                               : hs_launch_mirror(S, N_G, N_G, st);
-    if (e != cudaSuccess || (s_done && cudaEventRecord(s_done, st) != cudaSuccess)) rc = HS_ECUDA;
-  }
-  if (rc == HS_OK && timed && cudaEventRecord(ev[6], st) != cudaSuccess) rc = HS_ECUDA;
-  if (rc == HS_OK) {
-    // H = Z^H B + B^H Z + Y^H Y + A_f^H X_f
-    int n = 0;
-    P.seg[n++] = seg(SRC_Z, SRC_B, N_A);
-    P.seg[n++] = seg(SRC_B, SRC_Z, N_A);
-    if (N_h > 0) P.seg[n++] = seg(SRC_Y, SRC_Y, N_h);
-    if (N_f > 0) P.seg[n++] = seg(SRC_AF, SRC_X, N_f);
-    P.nseg = n;
-    P.C = H;
-    rc = launch_gemm(mode, s, tiles, smem, st, P);
-    if (rc == HS_OK && timed && cudaEventRecord(ev[7], st) != cudaSuccess) rc = HS_ECUDA;
-  }
-  delete PP;
-  return rc;
-}
-
-// The S contraction restricted to the lower-triangle tiles of row blocks [bi0, bi1):
-// they read only A and U.B slice rows below 128 * bi1, so a caller that slices column
-// chunks as they arrive can run them before the later chunks exist.
-int hs_plan_s::split_contract_S_rows(int N_G, double2* S, Workspace& w, cudaStream_t st, int bi0,
-                                     int bi1) {
-  const int s = slices;
-  const int rp = rows_pad_of(N_G, real);
-  const int mode = real ? MODE_CONTRACT_R : MODE_CONTRACT;
-  const int nbi = (N_G + BM - 1) / BM;
-  bi0 = std::max(bi0, 0);
-  bi1 = std::min(bi1, nbi);
-  if (bi1 <= bi0) return HS_OK;
-  int n_stage;
-  size_t smem;
-  int rc = split_geometry(n_stage, smem);
-  if (rc) return rc;
-  SplitParams* PP = new (std::nothrow) SplitParams;
-  if (!PP) return HS_ENOMEM;
-  SplitParams& P = *PP;
-  std::memset(&P, 0, sizeof(P));
-  int map_of[2][2];
-  int nm = 0;
-  bool ok = true;
-  for (int i = 0; i < 2 && ok; ++i) {
-    SliceBuf& b = w.sb[i == 0 ? SRC_A : SRC_UB];
-    const int nkb = kpad_of(N_A, N_L, real) / KB;
-    map_of[i][0] = nm;
-    ok = encode_left(&P.maps[nm++], b.plain, nkb, rp / 64, s, b.rot);
-    map_of[i][1] = nm;
-    ok = ok && encode_right(&P.maps[nm++], b.plain, nkb, rp / 64, s, b.rot);
-  }
-  if (!ok) {
-    delete PP;
-    return HS_ECUDA;
-  }
-  P.s = s;
-  P.N_G = N_G;
-  P.ldC = N_G;
-  P.nbj = (N_G + (real ? BN : BNC) - 1) / (real ? BN : BNC);
-  P.rows_pad = rp;
-  P.err = err_d;
-  int tiles = 0;
-  for (int b = bi0; b < bi1; ++b) tiles += 2 * std::min((real ? b / 2 : b) + 1, (P.nbj + 1) / 2);
-  P.bi0 = bi0;
-  P.nbi = bi1;
-  P.band = contract_band(mode, s, N_L, N_G);
-  P.ntiles = tiles;
-  for (int i = 0; i < 2; ++i) {
-    SplitSeg& g = P.seg[i];
-    g.mL = map_of[i][0];
-    g.mR = map_of[i][1];
-    g.kblocks = kpad_of(N_A, N_L, real) / KB;
-    g.eL = g.eR = w.sb[i == 0 ? SRC_A : SRC_UB].expo;
-  }
-  P.nseg = 2;
-  P.C = S;
-  const int stage_bytes = 4 * s * TILE_BYTES;
-  P.n_stage = tuned_depth(mode, s, N_L, N_G, n_stage, false, st, [](int) { return HS_OK; });
-  rc = launch_gemm(mode, s, tiles, smem_for(mode, P.n_stage, stage_bytes), st, P);
-  delete PP;
-  return rc;
-}
-
-int hs_plan_s::split_enqueue(const double2* A, const double2* B, int ldAB, const double* U,
-                             int N_G, double2* H, double2* S, Workspace& w, cudaStream_t st,
-                             bool timed, cudaEvent_t s_done, bool presliced, bool mirror) {
-  int rc = presliced ? HS_OK : split_inputs(A, B, ldAB, U, N_G, w, st, 0, -1, timed);
-  if (rc) return rc;
-  if (timed) HS_CUDA_TRY(cudaEventRecord(ev[9], st));
-  AtomsJob job{&w, N_G};
-  rc = split_atoms(&job, 1, st, nullptr);
-  if (rc) return rc;
-  return split_outputs(A, ldAB, N_G, H, S, w, st, timed, s_done, presliced, mirror);
-}
-
-// ---------------------------------------------------------------------------
-// hs_reduce on split plans: the two-sided transform C = L^{-1} H L^{-H} (Sec. 1.1) as
-// two BF16 slice contractions.  With B = L^{-H} (upper triangular) and Z = H B / 2,
-// C = Z^H B + B^H Z.  The full product H B comes from the lower triangle of M^H M for
-// the stacked operand M = [B | 0 | H] (n complex rows; B at columns [0, n), zeros up
-// to n_pad = rows_pad_of(n), H at [n_pad, n_pad + n)): below the split, its row blocks
-// hold H^H B = H B, K-major as the next contraction reads it.  Only those row blocks
-// are launched (bi0 = n_pad / BM), written through a base shifted back by n_pad rows.
-// The second contraction reads B's slices as M's first n rows.
-
-void hs_plan_s::split_reduce_release() {
-  for (SliceBuf* b : {&red_M, &red_Zs, &red_M2}) {
-    if (b->plain) cudaFree(b->plain);
-    if (b->expo) cudaFree(b->expo);
-    *b = SliceBuf{};
-  }
-  if (red_Z) cudaFree(red_Z);
-  if (red_half) cudaFree(red_half);
-  if (red_P2) cudaFree(red_P2);
-  if (red_Z2) cudaFree(red_Z2);
-  red_Z = red_Z2 = red_P2 = nullptr;
-  red_half = nullptr;
-  for (cudaEvent_t& e : red_pev)
-    if (e) cudaEventDestroy(e);
-  red_pev.clear();
-  red_split_cap = 0;
-}
-
-int hs_plan_s::split_reduce_alloc(int n) {
-  if (red_split_cap >= n) return HS_OK;
-  split_reduce_release();
-  if (!get_encode()) return HS_ECUDA;
-  const int n_pad = rows_pad_of(n), NM = n_pad + n;
-  const int rpM = rows_pad_of(NM), rp = rows_pad_of(n);
-  const size_t kpad = (size_t)kpad_of(n, 1);
-  const size_t oneM = (size_t)slices * rpM * kpad * 2, oneZ = (size_t)slices * rp * kpad * 2;
-  const bool ok =
-      cudaMalloc((void**)&red_M.plain, 2 * oneM) == cudaSuccess &&
-      cudaMalloc((void**)&red_M.expo, sizeof(int) * rpM) == cudaSuccess &&
-      cudaMalloc((void**)&red_Zs.plain, 2 * oneZ) == cudaSuccess &&
-      cudaMalloc((void**)&red_Zs.expo, sizeof(int) * rp) == cudaSuccess &&
-      cudaMalloc((void**)&red_Z, sizeof(double2) * (size_t)n * NM) == cudaSuccess &&
-      cudaMalloc((void**)&red_half, sizeof(double) * (size_t)n) == cudaSuccess &&
-      // the inverse's scratch: slices of K <= kRedPanel over up to n_pad + n columns,
-      // a kRedPanel x n transposed block, an n x (n_pad + n) product
-      cudaMalloc((void**)&red_M2.plain, (size_t)2 * slices * rpM * kpad_of(kRedPanel, 1) * 2) ==
-          cudaSuccess &&
-      cudaMalloc((void**)&red_M2.expo, sizeof(int) * rpM) == cudaSuccess &&
-      cudaMalloc((void**)&red_P2, sizeof(double2) * (size_t)kRedPanel * n) == cudaSuccess &&
-      cudaMalloc((void**)&red_Z2, sizeof(double2) * (size_t)n * NM) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    split_reduce_release();
-    return HS_ENOMEM;
-  }
-  std::vector<double> half((size_t)n, 0.5);
-  if (cudaMemcpy(red_half, half.data(), sizeof(double) * n, cudaMemcpyHostToDevice) !=
-      cudaSuccess) {
-    split_reduce_release();
-    return HS_ECUDA;
-  }
-  red_pev.assign((size_t)(n + kRedPanel - 1) / kRedPanel, nullptr);
-  for (cudaEvent_t& e : red_pev)
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-      split_reduce_release();
-      return HS_ECUDA;
-    }
-  red_M.rot = red_Zs.rot = red_M2.rot = true;  // plain and rotated slices interleaved
-  red_split_cap = n;
-  return HS_OK;
-}
-
-static int contract_tiles(const SplitParams& P) {
-  int tiles = 0;
-  for (int b = P.bi0; b < P.nbi; ++b) tiles += 2 * std::min(b + 1, (P.nbj + 1) / 2);
-  return tiles;
-}
-
-int hs_plan_s::split_reduce_transform(const double2* B, double2* H, int n, cudaStream_t st,
-                                      cudaEvent_t mid) {
-  if (precision != HS_SPLIT_BF16 || real || n < 1) return HS_EINVAL;
-  int rc = split_reduce_alloc(n);
-  if (rc) return rc;
-  const int s = slices;
-  const int n_pad = rows_pad_of(n), NM = n_pad + n;
-  const int rpM = rows_pad_of(NM), rp = rows_pad_of(n);
-  const int NKB = kpad_of(n, 1) / KB;
-  int n_stage;
-  size_t smem;
-  rc = split_geometry(n_stage, smem);
-  if (rc) return rc;
-  // 1. slices of M: B (zeros past column n up to n_pad), then H from column n_pad on (the
-  //    source pointer is shifted back so that column g reads H's column g - n_pad)
-  {
-    SliceParams sp{};
-    sp.job[0] = SliceJob{B, nullptr, red_M.plain, red_M.rot, red_M.expo, n, n};
-    rc = slice_launch(sp, 1, s, n, rpM, 1, false, st, 0, n_pad);
-    if (rc) return rc;
-    SliceParams sq{};
-    const double2* Hs =
-        (const double2*)((uintptr_t)H - (uintptr_t)n_pad * (uintptr_t)n * sizeof(double2));
-    sq.job[0] = SliceJob{Hs, nullptr, red_M.plain, red_M.rot, red_M.expo, n, n};
-    rc = slice_launch(sq, 1, s, NM, rpM, 1, false, st, n_pad, -1);
-    if (rc) return rc;
-  }
-  SplitParams* PP = new (std::nothrow) SplitParams;
-  if (!PP) return HS_ENOMEM;
-  std::unique_ptr<SplitParams> own(PP);
-  SplitParams& P = *PP;
-  // 2. H B: row blocks of M's H part against every column block up to the diagonal
-  std::memset(&P, 0, sizeof(P));
-  if (!encode_left(&P.maps[0], red_M.plain, NKB, rpM / 64, s, true) ||
-      !encode_right(&P.maps[1], red_M.plain, NKB, rpM / 64, s, true))
-    return HS_ECUDA;
-  P.seg[0] = SplitSeg{0, 1, NKB, red_M.expo, red_M.expo};
-  P.nseg = 1;
-  P.s = s;
-  P.N_G = NM;
-  P.ldC = n;
-  P.nbj = (NM + BNC - 1) / BNC;
-  P.rows_pad = rpM;
-  P.err = err_d;
-  P.bi0 = n_pad / BM;
-  P.nbi = (NM + BM - 1) / BM;
-  P.band = contract_band();
-  P.ntiles = contract_tiles(P);
-  P.C = (double2*)((uintptr_t)red_Z - (uintptr_t)n_pad * sizeof(double2));  // row n_pad -> 0
-  P.n_stage = n_stage;
-  rc = launch_gemm(MODE_CONTRACT, s, P.ntiles, smem, st, P);
-  if (rc) return rc;
-  if (mid && cudaEventRecord(mid, st) != cudaSuccess) return HS_ECUDA;
-  // 3. slices of Z = (H B) / 2: the first n columns of red_Z, halved by the row weight
-  {
-    SliceParams sz{};
-    sz.job[0] = SliceJob{red_Z, red_half, red_Zs.plain, red_Zs.rot, red_Zs.expo, n, n};
-    rc = slice_launch(sz, 1, s, n, rp, 1, false, st);
-    if (rc) return rc;
-  }
-  // 4. C = Z^H B + B^H Z, lower tiles, into H; then the mirror
-  std::memset(&P, 0, sizeof(P));
-  if (!encode_left(&P.maps[0], red_Zs.plain, NKB, rp / 64, s, true) ||
-      !encode_right(&P.maps[1], red_Zs.plain, NKB, rp / 64, s, true) ||
-      !encode_left(&P.maps[2], red_M.plain, NKB, rpM / 64, s, true) ||
-      !encode_right(&P.maps[3], red_M.plain, NKB, rpM / 64, s, true))
-    return HS_ECUDA;
-  P.seg[0] = SplitSeg{0, 3, NKB, red_Zs.expo, red_M.expo};  // Z^H B
-  P.seg[1] = SplitSeg{2, 1, NKB, red_M.expo, red_Zs.expo};  // B^H Z
-  P.nseg = 2;
-  P.s = s;
-  P.N_G = n;
-  P.ldC = n;
-  P.nbj = (n + BNC - 1) / BNC;
-  P.rows_pad = rp;
-  P.err = err_d;
-  P.bi0 = 0;
-  P.nbi = (n + BM - 1) / BM;
-  P.band = contract_band();
-  P.ntiles = contract_tiles(P);
-  P.C = H;
-  P.n_stage = n_stage;
-  rc = launch_gemm(MODE_CONTRACT, s, P.ntiles, smem, st, P);
-  if (rc) return rc;
-  return hs_launch_mirror(H, n, n, st) == cudaSuccess ? HS_OK : HS_ECUDA;
-}
-
-// ---------------------------------------------------------------------------
-// General products on the slice path for the blocked Cholesky and inverse of hs_reduce.
-// Operands are K-major (K complex rows x columns, column-major); red_M holds their
-// slices (its capacity, sized for the two-sided transform, covers K <= kRedPanel and
-// up to n_pad + n columns).
-
-// out = lower(X^H X) (nc x nc, leading dimension nc; whole lower tiles written).
-int hs_plan_s::split_herk_lower(const double2* X, int ldX, int K, int nc, double2* out,
-                                SliceBuf& sb, cudaStream_t st) {
-  const int s = slices, rp = rows_pad_of(nc), NKB = kpad_of(K, 1) / KB;
-  int n_stage;
-  size_t smem;
-  int rc = split_geometry(n_stage, smem);
-  if (rc) return rc;
-  SliceParams sp{};
-  sp.job[0] = SliceJob{X, nullptr, sb.plain, sb.rot, sb.expo, ldX, K};
-  rc = slice_launch(sp, 1, s, nc, rp, 1, false, st);
-  if (rc) return rc;
-  SplitParams* PP = new (std::nothrow) SplitParams;
-  if (!PP) return HS_ENOMEM;
-  std::unique_ptr<SplitParams> own(PP);
-  SplitParams& P = *PP;
-  std::memset(&P, 0, sizeof(P));
-  if (!encode_left(&P.maps[0], sb.plain, NKB, rp / 64, s, sb.rot) ||
-      !encode_right(&P.maps[1], sb.plain, NKB, rp / 64, s, sb.rot))
-    return HS_ECUDA;
-  P.seg[0] = SplitSeg{0, 1, NKB, sb.expo, sb.expo};
-  P.nseg = 1;
-  P.s = s;
-  P.N_G = nc;
-  P.ldC = nc;
-  P.nbj = (nc + BNC - 1) / BNC;
-  P.rows_pad = rp;
-  P.err = err_d;
-  P.bi0 = 0;
-  P.nbi = (nc + BM - 1) / BM;
-  P.band = contract_band();
-  P.ntiles = contract_tiles(P);
-  P.C = out;
-  P.n_stage = n_stage;
-  return launch_gemm(MODE_CONTRACT, s, P.ntiles, smem, st, P);
-}
-
-// out = A^H B (m x nc) for A (K x m) and B (K x nc): the block below the split of
-// lower(M^H M) for M = [B | 0 | A] (zeros from column nc up to nc_pad); out is
-// m x (nc_pad + m) with leading dimension m, the product in its first nc columns.
-int hs_plan_s::split_gemm_ahb(const double2* A, int ldA, int m, const double2* B, int ldB, int nc,
-                              int K, double2* out, SliceBuf& sb, cudaStream_t st) {
-  const int s = slices, nc_pad = rows_pad_of(nc), NM = nc_pad + m, rpM = rows_pad_of(NM);
-  const int NKB = kpad_of(K, 1) / KB;
-  int n_stage;
-  size_t smem;
-  int rc = split_geometry(n_stage, smem);
-  if (rc) return rc;
-  SliceParams sp{};
-  sp.job[0] = SliceJob{B, nullptr, sb.plain, sb.rot, sb.expo, ldB, K};
-  rc = slice_launch(sp, 1, s, nc, rpM, 1, false, st, 0, nc_pad);
-  if (rc) return rc;
-  SliceParams sq{};
-  const double2* As =
-      (const double2*)((uintptr_t)A - (uintptr_t)nc_pad * (uintptr_t)ldA * sizeof(double2));
-  sq.job[0] = SliceJob{As, nullptr, sb.plain, sb.rot, sb.expo, ldA, K};
-  rc = slice_launch(sq, 1, s, NM, rpM, 1, false, st, nc_pad, -1);
-  if (rc) return rc;
-  SplitParams* PP = new (std::nothrow) SplitParams;
-  if (!PP) return HS_ENOMEM;
-  std::unique_ptr<SplitParams> own(PP);
-  SplitParams& P = *PP;
-  std::memset(&P, 0, sizeof(P));
-  if (!encode_left(&P.maps[0], sb.plain, NKB, rpM / 64, s, sb.rot) ||
-      !encode_right(&P.maps[1], sb.plain, NKB, rpM / 64, s, sb.rot))
-    return HS_ECUDA;
-  P.seg[0] = SplitSeg{0, 1, NKB, sb.expo, sb.expo};
-  P.nseg = 1;
-  P.s = s;
-  P.N_G = NM;
-  P.ldC = m;
-  P.nbj = (NM + BNC - 1) / BNC;
-  P.rows_pad = rpM;
-  P.err = err_d;
-  P.bi0 = nc_pad / BM;
-  P.nbi = (NM + BM - 1) / BM;
-  P.band = contract_band();
-  P.ntiles = contract_tiles(P);
-  P.C = (double2*)((uintptr_t)out - (uintptr_t)nc_pad * sizeof(double2));  // row nc_pad -> 0
-  P.n_stage = n_stage;
-  return launch_gemm(MODE_CONTRACT, s, P.ntiles, smem, st, P);
-}
-
-// Right-looking Cholesky in panels of kRedPanel columns: each panel in FP64, then
-// S22 -= L21 L21^H = lower(X^H X) with X = L21^H on the slice path.
-int hs_plan_s::split_cholesky(double2* S, int n, int* fail, cudaStream_t st) {
-  int rc = split_reduce_alloc(n);
-  if (rc) return rc;
-  for (int j0 = 0; j0 < n; j0 += kRedPanel) {
-    const int pw = std::min(kRedPanel, n - j0);
-    if (hs_launch_cholesky_panel(S, n, j0, pw, fail, st) != cudaSuccess) return HS_ECUDA;
-    // panel j0 / kRedPanel of L is final: later updates touch columns right of it only
-    if (cudaEventRecord(red_pev[j0 / kRedPanel], st) != cudaSuccess) return HS_ECUDA;
-    const int r0 = j0 + pw, n2 = n - r0;
-    if (n2 <= 0) break;
-    double2* X = red_P;  // pw x n2, leading dimension pw
-    if (hs_launch_ctrans(S + (size_t)r0 + (size_t)j0 * n, n, n2, pw, X, pw, st) != cudaSuccess)
-      return HS_ECUDA;
-    rc = split_herk_lower(X, pw, pw, n2, red_Z, red_M, st);
-    if (rc) return rc;
-    if (hs_launch_sub(S + (size_t)r0 + (size_t)r0 * n, n, red_Z, n2, n2, n2, 1, fail, st) !=
-        cudaSuccess)
-      return HS_ECUDA;
-  }
-  return hs_launch_zero_upper(S, n, fail, st) == cudaSuccess ? HS_OK : HS_ECUDA;
-}
-
-// Forward substitution L W = I in block rows of kRedPanel: each block row in FP64,
-// then W[r0 :, 0 : ncols] -= L[r0 :, i0 : i0 + pw] W[i0 : i0 + pw, 0 : ncols] on the
-// slice path (A = that block of L, conjugate-transposed to K-major).  Block row i reads
-// L's panel i only: it starts once split_cholesky has recorded that panel's event.
-int hs_plan_s::split_inverse(const double2* L, double2* W, int n, const int* fail,
-                             cudaStream_t st) {
-  int rc = split_reduce_alloc(n);
-  if (rc) return rc;
-  if (hs_launch_eye(W, n, fail, st) != cudaSuccess) return HS_ECUDA;
-  for (int i0 = 0; i0 < n; i0 += kRedPanel) {
-    const int pw = std::min(kRedPanel, n - i0);
-    if (cudaStreamWaitEvent(st, red_pev[i0 / kRedPanel], 0) != cudaSuccess) return HS_ECUDA;
-    if (hs_launch_inverse_blockrow(L, W, n, i0, pw, fail, st) != cudaSuccess) return HS_ECUDA;
-    const int r0 = i0 + pw, m = n - r0, ncols = i0 + pw;
-    if (m <= 0) break;
-    double2* A = red_P2;  // pw x m, leading dimension pw
-    if (hs_launch_ctrans(L + (size_t)r0 + (size_t)i0 * n, n, m, pw, A, pw, st) != cudaSuccess)
-      return HS_ECUDA;
-    rc = split_gemm_ahb(A, pw, m, W + i0, n, ncols, pw, red_Z2, red_M2, st);
-    if (rc) return rc;
-    if (hs_launch_sub(W + r0, n, red_Z2, m, m, ncols, 0, fail, st) != cudaSuccess)
-      return HS_ECUDA;
-  }
-  return HS_OK;
-}
+}  // namespace hs_split
