@@ -39,6 +39,17 @@ by ``1 / (1 + l)``) from torch's counter-based (Philox) CUDA generator seeded wi
 stream from the host draws, so the values differ; the shapes, distributions and
 structure are the same.
 
+Matching-coefficient inputs (``matching_inputs``; Sec. 1.1: the basis functions are
+plane waves e^{i(k+G).r} outside the muffin-tin spheres and radial functions times
+spherical harmonics inside): a cubic cell of side ``a`` with volume ``Omega = a^3``
+sized so that N_G plane waves reach |k+G| <= K_max = (l_max + 1) / 2.2 (the usual
+R K_max ~ l_max balance); a k-point uniform in the Brillouin zone; the N_G vectors
+k + G (G on the reciprocal lattice of spacing 2 pi / a) of smallest length; atom
+positions uniform in the cell; sphere radii R uniform in [1.6, 2.2]; per (atom, l)
+radial boundary values u(R) ~ U[0.5, 1.5], u'(R) ~ U[-1, 1], udot(R) ~ U[-0.5, 0.5]
+and udot'(R) chosen so that the Wronskian u udot' - u' udot equals 1 / R^2 (the
+normalisation of a radial function and its energy derivative), tensor ids 30-33.
+
 Indefinite atoms: ``n_f = round(frac * N_A)`` atoms at
 ``(3 + floor(i * N_A / n_f)) mod N_A`` for ``i < n_f``.
 
@@ -266,6 +277,39 @@ def make_inputs_device(w: Workload, device):
     T_AA, T_AB, T_BB = t_matrices(w.N_A, w.N_L, w.indefinite, w.seed)
     U = u_norms(w.N_A, w.N_L, w.seed)
     return dict(A=A, B=B, T_AA=T_AA, T_AB=T_AB, T_BB=T_BB, U=U)
+
+
+_ID_KPT, _ID_TAU, _ID_RMT, _ID_UFUN = 30, 31, 32, 33
+
+
+def matching_inputs(N_A: int, l_max: int, N_G: int, seed: int = 0):
+    """Inputs of the matching step: dict with Kvec (N_G, 3) wave vectors k + G, tau
+    (N_A, 3) atom positions, R (N_A,) sphere radii, ufun (N_A, l_max + 1, 4) radial
+    boundary values u, u', udot, udot' at R, omega (cell volume), a (cell side)."""
+    K_max = (l_max + 1) / 2.2
+    omega = 6.0 * math.pi ** 2 * N_G / K_max ** 3  # N_G ~ Omega K_max^3 / (6 pi^2)
+    a = omega ** (1.0 / 3.0)
+    b = 2.0 * math.pi / a
+    k = (_rng(seed, _ID_KPT).uniform(-0.5, 0.5, size=3)) * b
+    nmax = int(math.ceil(K_max / b)) + 3
+    while True:
+        r = np.arange(-nmax, nmax + 1)
+        n = np.stack(np.meshgrid(r, r, r, indexing="ij"), axis=-1).reshape(-1, 3)
+        K = k[None, :] + b * n
+        if len(K) >= 2 * N_G:
+            break
+        nmax += 2
+    order = np.argsort(np.linalg.norm(K, axis=1), kind="stable")
+    Kvec = K[order[:N_G]]
+    tau = _rng(seed, _ID_TAU).uniform(0.0, 1.0, size=(N_A, 3)) * a
+    R = _rng(seed, _ID_RMT).uniform(1.6, 2.2, size=N_A)
+    g = _rng(seed, _ID_UFUN)
+    u = g.uniform(0.5, 1.5, size=(N_A, l_max + 1))
+    du = g.uniform(-1.0, 1.0, size=(N_A, l_max + 1))
+    ud = g.uniform(-0.5, 0.5, size=(N_A, l_max + 1))
+    dud = (1.0 / R[:, None] ** 2 + du * ud) / u  # Wronskian u udot' - u' udot = 1 / R^2
+    ufun = np.stack([u, du, ud, dud], axis=-1)
+    return dict(Kvec=Kvec, tau=tau, R=R, ufun=ufun, omega=omega, a=a)
 
 
 def as_colmajor_T(T: np.ndarray) -> np.ndarray:
