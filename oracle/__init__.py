@@ -15,4 +15,3 @@ orthonormality).
 from .hs_oracle import assemble, h_aa, rel_frobenius  # noqa: F401
 from .cholesky import cholesky_lower, fail_flags  # noqa: F401
 from .reduce import reduce_standard, standard_eigenvalues  # noqa: F401
-from .matching import matching, ylm  # noqa: F401
