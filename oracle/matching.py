@@ -29,7 +29,8 @@ and of its (radial) derivative on the sphere boundary r_a = R_a.  Written out:
 
 Y_lm are the orthonormal complex spherical harmonics with the Condon-Shortley phase,
 written out from their definition (Ferrers functions from the derivatives of the
-Legendre polynomial, no library routine); the spherical Bessel functions j_l and j_l'
+Legendre polynomial, differentiated and evaluated in the Legendre basis; no
+spherical-harmonic library routine); the spherical Bessel functions j_l and j_l'
 are scipy's.  The row of (l, m) in a block of N_L = (l_max + 1)^2 rows is
 L = l^2 + l + m, the order the assembly uses (angular momentum l = floor(sqrt(L))).
 """
@@ -66,10 +67,11 @@ def ylm(l_max: int, theta, phi) -> np.ndarray:
     for l in range(l_max + 1):
         P = np.zeros(l + 1)
         P[l] = 1.0  # P_l in the Legendre basis
-        Pl_poly = npleg.leg2poly(P)  # power-series coefficients of P_l
         for m in range(0, l + 1):
-            dm = np.polynomial.polynomial.polyder(Pl_poly, m) if m > 0 else Pl_poly
-            Plm = sin_t ** m * np.polynomial.polynomial.polyval(x, dm)
+            # d^m P_l / dx^m kept in the Legendre basis and summed there (Clenshaw): the
+            # power-series form of the same polynomial cancels to ~1e-12 at l = 11
+            dm = npleg.legder(P, m) if m > 0 else P
+            Plm = sin_t ** m * npleg.legval(x, dm)
             norm = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - m)
                              / math.factorial(l + m))
             Ypos = (-1) ** m * norm * Plm * np.exp(1j * m * phi)

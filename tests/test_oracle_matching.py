@@ -72,6 +72,30 @@ def test_ylm_matches_scipy_when_available():
         assert np.allclose(Y[l * l + l + m], sp.sph_harm_y(l, m, th, ph), atol=1e-13)
 
 
+def test_ylm_and_bessel_against_40_digit_values():
+    """Y_lm up to l = 11 (the largest l the assembly takes) and j_l, j_l' at the x range
+    of the workloads, against mpmath at 40 digits: pins the accuracy the parity tests
+    rely on (1e-14 absolute on Y, 1e-14 relative on j_l, 5e-14 on j_l')."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    _, th, ph = _sphere_points(12, 3)
+    Y = om.ylm(11, th, ph)
+    for L, (l, m) in enumerate(om.lm_of_L(144)):
+        for k in range(0, 12, 3):
+            t = complex(mpmath.spherharm(l, m, mpmath.mpf(float(th[k])),
+                                         mpmath.mpf(float(ph[k]))))
+            assert abs(Y[L, k] - t) < 1e-14, (l, m, k)
+    for x in (0.37, 2.9, 7.3, 12.0):
+        X = mpmath.mpf(x)
+        for l in range(12):
+            jl = mpmath.sqrt(mpmath.pi / (2 * X)) * mpmath.besselj(l + mpmath.mpf(1) / 2, X)
+            jn = mpmath.sqrt(mpmath.pi / (2 * X)) * mpmath.besselj(l + mpmath.mpf(3) / 2, X)
+            assert abs(spherical_jn(l, x) - float(jl)) <= 1e-14 * abs(float(jl))
+            djl = float(l / X * jl - jn)
+            # scipy's j_l' = j_{l-1} - (l + 1) / x j_l cancels at small x: ~1.5e-14 at l = 11
+            assert abs(spherical_jn(l, x, derivative=True) - djl) <= 5e-14 * abs(djl)
+
+
 def test_spherical_bessel_closed_forms():
     x = np.linspace(0.1, 12.0, 37)
     j0 = np.sin(x) / x
