@@ -22,6 +22,8 @@ The JSON line carries:
   (host-to-device copies of A, B, T, U and the copy back of H, S inside the timed
   region);
 * ``split_8000``: the split form on ``split_8000`` (N_A=100, N_L=121, N_G=8000);
+* ``matching``: ``hs_matching`` (the matching coefficients A, B of Sec. 1.1) at the
+  workload's N_A, l_max and N_G, with its HBM-store and FP64 roofline fractions;
 * ``cpu_baseline``: the FP64 oracle on the host cores on a column panel, scaled to
   a full k-point, and the sampled error of both forms on that panel;
 * ``serving``: ``hs_submit`` / ``hs_poll`` continuous batching (N_A=64, N_L=81,
@@ -44,6 +46,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -573,6 +576,60 @@ def _relaunch_under_torchrun(args) -> int:
     return subprocess.call(cmd)
 
 
+def matching_block(args, w, dev, stream, barrier) -> dict:
+    """hs_matching (Sec. 1.1) at the workload's N_A, l_max = sqrt(N_L) - 1 and N_G: its
+    A and B (2 K N_G complex doubles) written to HBM.  The kernel is bound by its FP64
+    arithmetic or by the stores; both fractions are reported."""
+    import torch
+    from paper_1611_00606_gb300 import hs
+    l_max = int(round(math.sqrt(w.N_L))) - 1
+    if (l_max + 1) ** 2 != w.N_L or l_max > 11:
+        return None
+    _, rank, _ = _dist()
+    d = synth.matching_inputs(w.N_A, l_max, w.N_G, seed=w.seed + rank)
+    t = {k: torch.from_numpy(np.ascontiguousarray(d[k])).to(dev)
+         for k in ("Kvec", "tau", "R", "ufun")}
+    K = w.K
+    A = torch.empty((w.N_G, K), dtype=torch.complex128, device=dev).T
+    B = torch.empty((w.N_G, K), dtype=torch.complex128, device=dev).T
+
+    def one():
+        hs.hs_matching(t["Kvec"], t["tau"], t["R"], t["ufun"], d["omega"], l_max, A, B,
+                       stream)
+    for _ in range(3):
+        one()
+    steps = max(3, args.steps // 2)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = reduce_max(e0.elapsed_time(e1), dev) / steps
+    del A, B
+    peaks, peak_src = _peaks()
+    nbytes = 2 * 16 * K * w.N_G  # A and B stored once; inputs are O(N_G + N_A l_max)
+    # per output row (a, L) of a column: e^{iK.tau} c_L (complex product, 6 flops), times
+    # the two real radial factors (4 flops)
+    flops = 10 * K * w.N_G
+    gbs = nbytes / (ms / 1e3) / 1e9
+    tf = flops / (ms / 1e3) / 1e12
+    return {"workload": f"N_A={w.N_A}, l_max={l_max} (N_L={w.N_L}), N_G={w.N_G}",
+            "ms_per_call": ms, "steps": steps, "columns_per_s": w.N_G / (ms / 1e3),
+            "roofline": {"hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                 "frac": gbs / peaks["hbm_gbs"],
+                                 "work": "A and B stored once (32 bytes per row and column)",
+                                 "peak_source": f"hbm_gbs ({peak_src})"},
+                         "fp64": {"achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                  "frac": tf / FP64_PEAK_TFLOPS,
+                                  "work": "10 FP64 flops per row and column",
+                                  "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"}},
+            "gpu_launches": steps}
+
+
 def run_main(args, w):
     import torch
     ws, rank, local = _dist()
@@ -772,6 +829,12 @@ def run_main(args, w):
         del d3, T3, U3, H3, S3
         torch.cuda.empty_cache()
 
+    # ---------------- matching coefficients A, B of this workload's shape (hs_matching)
+    matching = None
+    if not args.no_matching:
+        matching = matching_block(args, w, dev, stream, barrier)
+        torch.cuda.empty_cache()
+
     # ---------------- serving (N=1)
     serving = None
     if ws == 1 and split and not args.no_serve:
@@ -796,6 +859,7 @@ def run_main(args, w):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "split_8000": c3,
+            "matching": matching,
             "serving": serving,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
@@ -890,6 +954,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-side", action="store_true", help="skip the split_8000 line item")
+    ap.add_argument("--no-matching", action="store_true",
+                    help="skip the matching-coefficient (hs_matching) line item")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving object")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of each split-form serving run of the main line")

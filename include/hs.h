@@ -265,6 +265,33 @@ int hs_reduce(hs_plan_t plan, hs_z* H, hs_z* S, int N_G, hs_reduce_info* info);
  * HS_ENOTSUP; complex plans: HS_EINVAL.  HS_ENOTPD leaves H and S unchanged. */
 int hs_reduce_real(hs_plan_t plan, double* H, double* S, int N_G, hs_reduce_info* info);
 
+/* ---------------------------------------------------------------------------
+ * Matching coefficients A, B (the inputs of hs_assemble), Sec. 1.1.  The basis
+ * function of plane wave g, wave vector K_g = k + G_g, is e^{i K.r} / sqrt(Omega)
+ * between the spheres and, in the sphere of atom a (centre tau_a, radius R_a),
+ *   sum_{l,m} [A_{aL,g} u^a_l(r) + B_{aL,g} udot^a_l(r)] Y_lm(r^),   L = l^2 + l + m;
+ * A and B make the function and its radial derivative continuous at r = R_a.  With
+ * the Rayleigh expansion of the plane wave,
+ *   c = (4 pi / sqrt(Omega)) e^{i K.tau_a} i^l conj(Y_lm(K^)),   x = |K| R_a,
+ *   A = c (j_l(x) udot'_l - |K| j_l'(x) udot_l) / W,
+ *   B = c (|K| j_l'(x) u_l - j_l(x) u'_l) / W,      W = u_l udot'_l - u'_l udot_l,
+ * Y_lm orthonormal with the Condon-Shortley phase, j_l spherical Bessel functions;
+ * a zero K takes the direction theta = phi = 0.
+ * Inputs (DEVICE pointers, doubles, row-major):
+ *   Kvec : N_G x 3 Cartesian wave vectors k + G;   tau : N_A x 3 atom positions;
+ *   R    : N_A sphere radii;
+ *   ufun : N_A x (l_max + 1) x 4 radial boundary values at R_a, in the order
+ *          u_l(R), u_l'(R), udot_l(R), udot_l'(R);   omega : cell volume (> 0).
+ * Outputs: A, B (distinct, not overlapping the inputs) in the layout of hs_assemble,
+ *   (N_A N_L) x N_G column-major with leading dimension ld_AB >= N_A N_L; only rows
+ *   [0, N_A N_L) of each column are written.
+ * 0 <= l_max <= 11 (N_L <= 144); N_G = 0 returns HS_OK at once.  A zero W gives
+ * non-finite coefficients (not checked).  stream is a cudaStream_t (NULL = legacy
+ * default stream); the call returns after A and B are complete. */
+int hs_matching(const double* Kvec, const double* tau, const double* R, const double* ufun,
+                double omega, int N_A, int l_max, int N_G, hs_z* A, hs_z* B, int ld_AB,
+                void* stream);
+
 /* Static description of an error code. */
 const char* hs_strerror(int code);
 

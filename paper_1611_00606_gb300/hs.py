@@ -77,6 +77,7 @@ SIGNATURES = {
                               C.POINTER(hs_info)]),
     "hs_reduce": (_I, [_VP, _VP, _VP, _I, C.POINTER(hs_reduce_info)]),
     "hs_reduce_real": (_I, [_VP, _VP, _VP, _I, C.POINTER(hs_reduce_info)]),
+    "hs_matching": (_I, [_VP, _VP, _VP, _VP, C.c_double, _I, _I, _I, _VP, _VP, _I, _VP]),
 }
 
 
@@ -297,6 +298,42 @@ def hs_assemble_static(A, B, T_AA, T_AB, T_BB, U, N_A: int, N_L: int, N_G: int, 
     _check(_lib.hs_assemble_static(_ptr(A), _ptr(B), _ptr(T_AA), _ptr(T_AB), _ptr(T_BB),
                                    _ptr(U), N_A, N_L, N_G, _ptr(H), _ptr(S),
                                    C.c_void_p(stream.cuda_stream)), "hs_assemble_static")
+
+
+def _check_f64(X, shape, name):
+    import torch
+    if X.dtype != torch.float64 or not X.is_cuda or tuple(X.shape) != shape or \
+            not X.is_contiguous():
+        raise ValueError(f"{name}: contiguous float64 CUDA tensor of shape {shape} required")
+
+
+def hs_matching(Kvec, tau, R, ufun, omega: float, l_max: int, A=None, B=None,
+                stream=None):
+    """Matching coefficients A, B (Sec. 1.1) of N_G plane waves (Kvec: (N_G, 3)) on N_A
+    spheres (tau: (N_A, 3), R: (N_A,), ufun: (N_A, l_max + 1, 4) = u, u', udot, udot'
+    at R), float64 CUDA tensors.  Returns A, B as (N_A N_L, N_G) column-major complex128
+    tensors, allocated here unless given (any leading dimension >= N_A N_L)."""
+    import torch
+    N_G, N_A = int(Kvec.shape[0]), int(tau.shape[0])
+    N_L = (l_max + 1) ** 2
+    K = N_A * N_L
+    _check_f64(Kvec, (N_G, 3), "Kvec")
+    _check_f64(tau, (N_A, 3), "tau")
+    _check_f64(R, (N_A,), "R")
+    _check_f64(ufun, (N_A, l_max + 1, 4), "ufun")
+    if A is None:
+        A = torch.empty((N_G, K), dtype=torch.complex128, device=Kvec.device).T
+    if B is None:
+        B = torch.empty((N_G, K), dtype=torch.complex128, device=Kvec.device).T
+    ld = _check_coef(A, K, N_G, "A")
+    if _check_coef(B, K, N_G, "B") != ld:
+        raise ValueError("hs_matching: A and B must share one leading dimension")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(_lib.hs_matching(_ptr(Kvec), _ptr(tau), _ptr(R), _ptr(ufun), float(omega), N_A,
+                            l_max, N_G, _ptr(A), _ptr(B), ld, C.c_void_p(stream.cuda_stream)),
+           "hs_matching")
+    return A, B
 
 
 # ---------------------------------------------------------------- real-symmetric variant
