@@ -39,7 +39,8 @@ no collective on the data path); serving runs at N=1 only.
 column panel of the same workload per step (the only other use of oracle/).
 ``--real`` measures the real-symmetric variant (``hs_assemble_real``),
 ``--reduce`` the generalized-eigenproblem reduction (``hs_reduce``) on the H, S the
-split assembly produces, ``--serve`` the serving loop alone; these take
+split assembly produces, ``--serve`` the serving loop alone, ``--matching`` the
+matching coefficients alone (at the default workload's shape); the first two take
 ``auag_like_4000`` unless ``--workload`` says otherwise.
 """
 from __future__ import annotations
@@ -630,6 +631,19 @@ def matching_block(args, w, dev, stream, barrier) -> dict:
             "gpu_launches": steps}
 
 
+def run_matching(args, w):
+    """``--matching``: the matching-coefficient line item alone (N=1)."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    clk = ClockSampler(0)
+    clk.start()
+    r = matching_block(args, w, dev, torch.cuda.current_stream(), lambda: None)
+    r["clocks"] = clk.stop()
+    print(json.dumps(r))
+    return 0
+
+
 def run_main(args, w):
     import torch
     ws, rank, local = _dist()
@@ -968,6 +982,8 @@ def main():
                     help="generalized-eigenproblem reduction (hs_reduce) of the workload's H, S")
     ap.add_argument("--real", action="store_true",
                     help="real-symmetric variant (hs_assemble_real) on real inputs of the workload")
+    ap.add_argument("--matching", action="store_true",
+                    help="matching coefficients (hs_matching) alone at the workload's shape")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=0.0, help="Poisson arrivals per s (0: all at t=0)")
     ap.add_argument("--pool", type=int, default=4)
@@ -992,6 +1008,8 @@ def main():
         return run_reference(args, w)
     if args.ksplit:
         return run_ksplit(args, w)
+    if args.matching:
+        return run_matching(args, w)
     return run_main(args, w)
 
 

@@ -8,12 +8,22 @@
 //   B = c_lm (K j_l'(KR) u(R) - j_l(KR) u'(R)) / W,   W = u udot' - u' udot,
 // with j_l the spherical Bessel functions (K = |K|).
 //
-// One CTA per plane wave g: the angular factors c_lm / e^{i K.tau_a} of the column in
-// shared memory (normalised associated Legendre functions by the standard l recurrence,
-// Condon-Shortley phase), then per chunk of atoms the phases and the radial factors
-// (j_l for all l by Miller's downward recurrence, normalised to j_0 or j_1), then the
-// column's K = N_A N_L rows of A and B, which are contiguous in the column-major
-// layout, written by consecutive threads.
+// GB300 runs FP64 at 2 operations per clock per SM, so this kernel is bound by its
+// FP64 arithmetic, not by the stores of A and B; it is arranged to spend as few FP64
+// operations per output element as the formula allows.  With conj(Y_lm) written as
+// N_l|m| P_l^|m|(cos theta) e^{-i m phi} (times (-1)^m for m < 0), each element is the
+// product of three factors, two of them real:
+//   A_{aL} = [e^{i K.tau_a} e^{-i m phi}] * [i^l pref sigma N P]_L * f^A_{al},
+// the complex one per (atom, m), the real one per row L, the radial one per (atom, l)
+// and shared with B (f^B in place of f^A): 2 products for X = E * P_L, the factor i^l
+// applied as a sign and a swap, then 2 products each for A and B.
+//
+// One CTA per plane wave g, all atoms: the per-row factors P_L and e^{-i m phi} in
+// shared memory (normalised associated Legendre functions by their l recurrence with
+// compile-time coefficients, Condon-Shortley phase), then per chunk of atoms one thread per atom computes
+// E_{a,m} and the radial factors (j_l for all l by Miller's downward recurrence,
+// normalised to j_0 or j_1), then the column's rows of the chunk, contiguous in the
+// column-major layout, are written by consecutive threads.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -22,18 +32,62 @@
 
 namespace {
 
-constexpr int kMaxL = 11;               // l_max: (l_max + 1)^2 <= 168 rows per atom
+constexpr int kMaxL = 11;               // l_max: (l_max + 1)^2 <= 144 rows per atom
 constexpr int kMaxNL = (kMaxL + 1) * (kMaxL + 1);
-constexpr int kAtomChunk = 64;          // atoms whose radial factors sit in smem at once
+constexpr int kMaxM = 2 * kMaxL + 1;    // m = -l_max .. l_max
+constexpr int kAtomChunk = 64;          // atoms whose factors sit in smem at once
 constexpr int kThreads = 256;
 
+// ---- constant tables of the normalised associated Legendre functions
+// Pbar_lm = N_lm P_lm (Condon-Shortley phase), N_lm = sqrt((2l + 1) / (4 pi) (l - m)! / (l + m)!),
+// obey (standard recurrences, from the ones of P_lm with the ratios of the N_lm):
+//   Pbar_00 = 1 / sqrt(4 pi),   Pbar_mm = c_m sin(theta) Pbar_{m-1,m-1},  c_m = -sqrt((2m + 1) / (2m)),
+//   Pbar_lm = a_lm (cos(theta) Pbar_{l-1,m} - b_lm Pbar_{l-2,m})  (l > m, Pbar_{m-1,m} = 0),
+//   a_lm = sqrt((4 l^2 - 1) / (l^2 - m^2)),  b_lm = sqrt(((l - 1)^2 - m^2) / (4 (l - 1)^2 - 1)).
+// The coefficients are evaluated at compile time (Newton's iteration for the square
+// root, run until it stops decreasing: within an ulp), so the kernel spends no FP64
+// divisions or square roots on them.
+constexpr double ce_sqrt(double x) {
+  if (x <= 0.0) return 0.0;
+  double r = x > 1.0 ? x : 1.0;  // start above sqrt(x): Newton then decreases monotonically
+  for (int i = 0; i < 2000; ++i) {
+    const double n = 0.5 * (r + x / r);
+    if (!(n < r)) break;
+    r = n;
+  }
+  return r;
+}
+
+struct LegendreTab {
+  double a[kMaxNL], b[kMaxNL];  // at index l^2 + l + m, 0 <= m < l
+  double c[kMaxL + 1];          // c_m, m >= 1
+  double p00;
+};
+
+constexpr LegendreTab make_legendre_tab() {
+  LegendreTab t{};
+  for (int l = 0; l <= kMaxL; ++l) {
+    for (int m = 0; m < l; ++m) {
+      const double l2 = (double)l * l, m2 = (double)m * m, lm1 = l - 1.0;
+      t.a[l * l + l + m] = ce_sqrt((4.0 * l2 - 1.0) / (l2 - m2));
+      t.b[l * l + l + m] = ce_sqrt((lm1 * lm1 - m2) / (4.0 * lm1 * lm1 - 1.0));
+    }
+  }
+  for (int m = 1; m <= kMaxL; ++m) t.c[m] = -ce_sqrt((2.0 * m + 1.0) / (2.0 * m));
+  t.p00 = 1.0 / ce_sqrt(4.0 * 3.14159265358979323846);
+  return t;
+}
+
+__constant__ LegendreTab kLeg = make_legendre_tab();
+
 // j_l(x) for l = 0 .. lmax (x >= 0) and j_l'(x).  Miller's method: the recurrence
-// f_{n-1} = (2n + 1) / x f_n - f_{n+1}, run downwards from n0 = m + 8 + sqrt(40 m),
-// m = max(lmax, x) (where j_n decays fast in n), is stable; the sequence is rescaled
-// when it nears overflow and normalised by whichever of j_0 = sin x / x and
-// j_1 = sin x / x^2 - cos x / x is larger in magnitude.  j_l' = (l / x) j_l - j_{l+1}.
+// f_{n-1} = (2n + 1) / x f_n - f_{n+1}, run downwards from
+// n0 = max(lmax + x + 6, x + 4.5 sqrt(x) + 6) (where j_n decays fast in n), is stable;
+// the sequence is rescaled when it nears overflow and normalised by whichever of
+// j_0 = sin x / x and j_1 = sin x / x^2 - cos x / x is larger in magnitude;
+// j_l' = (l / x) j_l - j_{l+1}.
 __device__ void sph_bessel(double x, int lmax, double* j, double* dj) {
-  if (x == 0.0) {
+  if (x < 1e-30) {  // j_l(x) = x^l / (2l + 1)!! (1 + O(x^2)): below 1e-30 of j_0 for l > 0
     for (int l = 0; l <= lmax; ++l) {
       j[l] = l == 0 ? 1.0 : 0.0;
       dj[l] = l == 1 ? 1.0 / 3.0 : 0.0;
@@ -42,18 +96,20 @@ __device__ void sph_bessel(double x, int lmax, double* j, double* dj) {
   }
   double f[kMaxL + 2];
   for (int l = 0; l < kMaxL + 2; ++l) f[l] = 0.0;
-  const double m = fmax((double)lmax, x);
-  const int n0 = (int)(m + 8.0 + sqrt(40.0 * m));
-  const double rx = 1.0 / x;
-  double fp1 = 0.0, fn = 1e-200;  // f_{n+1}, f_n
+  const int n0 = (int)fmax(lmax + x + 6.0, x + 4.5 * sqrt(x) + 6.0);
+  const double rx = 1.0 / x, rx2 = 2.0 * rx;
+  double coef = (2.0 * n0 + 1.0) * rx;  // (2n + 1) / x, stepped down by 2 / x
+  double fp1 = 0.0, fn = 1e-200;        // f_{n+1}, f_n
   for (int n = n0; n >= 1; --n) {
-    const double fm1 = (2.0 * n + 1.0) * rx * fn - fp1;
+    const double fm1 = coef * fn - fp1;
+    coef -= rx2;
     fp1 = fn;
     fn = fm1;
-    if (fabs(fn) > 1e200) {  // rescale the sequence, the part kept so far included
-      fp1 *= 1e-200;
-      fn *= 1e-200;
-      for (int l = 0; l < kMaxL + 2; ++l) f[l] *= 1e-200;
+    // rescale when |f| passes 2^664 (exponent field of the high word: no FP64 compare)
+    if (((__double2hiint(fn) >> 20) & 0x7ff) > 1023 + 664) {
+      fp1 *= 0x1p-1328;
+      fn *= 0x1p-1328;
+      for (int l = 0; l < kMaxL + 2; ++l) f[l] *= 0x1p-1328;
     }
     if (n - 1 <= lmax + 1) f[n - 1] = fn;
   }
@@ -72,17 +128,19 @@ __global__ void __launch_bounds__(kThreads) k_matching(const double* __restrict_
                                                        const double* __restrict__ tau,
                                                        const double* __restrict__ R,
                                                        const double* __restrict__ ufun,
-                                                       double pref, int N_A, int lmax, int N_G, size_t ld,
-                                                       double2* __restrict__ A,
+                                                       double pref, int N_A, int lmax, int N_G,
+                                                       size_t ld, double2* __restrict__ A,
                                                        double2* __restrict__ B) {
-  __shared__ double2 c_L[kMaxNL];               // (4 pi / sqrt(Omega)) i^l conj(Y_lm(K^))
-  __shared__ unsigned char l_of[kMaxNL];
-  __shared__ double2 ph[kAtomChunk];            // e^{i K.tau_a}
-  __shared__ double fa[kAtomChunk][kMaxL + 1];  // radial factor of A
-  __shared__ double fb[kAtomChunk][kMaxL + 1];  // radial factor of B
+  __shared__ double P_L[kMaxNL];                // (-1)^{floor(l/2)} pref sigma_m Pbar, real
+  __shared__ unsigned char l_of[kMaxNL], mi_of[kMaxNL];
+  __shared__ double2 w_m[kMaxM];                // e^{-i m phi} at index lmax + m
+  __shared__ double2 E[kAtomChunk][kMaxM];      // e^{i K.tau_a} e^{-i m phi}
+  __shared__ double fa[kAtomChunk][kMaxL + 1];  // radial factor of A (over W)
+  __shared__ double fb[kAtomChunk][kMaxL + 1];  // radial factor of B (over W)
   const int g = blockIdx.x;
   if (g >= N_G) return;
   const int N_L = (lmax + 1) * (lmax + 1);
+  const int NM = 2 * lmax + 1;
   const double kx = Kvec[3 * g], ky = Kvec[3 * g + 1], kz = Kvec[3 * g + 2];
   const double rho = sqrt(kx * kx + ky * ky);
   const double Kn = sqrt(rho * rho + kz * kz);
@@ -90,83 +148,93 @@ __global__ void __launch_bounds__(kThreads) k_matching(const double* __restrict_
   const double ct = Kn > 0.0 ? kz / Kn : 1.0, st = Kn > 0.0 ? rho / Kn : 0.0;
   const double cp = rho > 0.0 ? kx / rho : 1.0, sp = rho > 0.0 ? ky / rho : 0.0;
 
-  // ---- angular factors: thread m runs the l recurrence of order m
+  // ---- per-row factors: thread m runs the l recurrence of order m
   if (threadIdx.x <= lmax) {
     const int m = threadIdx.x;
-    // P_mm = (-1)^m (2m - 1)!! sin^m theta (Condon-Shortley phase included)
-    double pmm = 1.0;
-    for (int i = 1; i <= m; ++i) pmm *= -(2.0 * i - 1.0) * st;
-    // e^{i m phi}
+    // Pbar_mm from Pbar_00 by the c_m steps
+    double pmm = kLeg.p00;
+    for (int i = 1; i <= m; ++i) pmm *= kLeg.c[i] * st;
+    // e^{i m phi} by repeated rotation; e^{-i m phi} is its conjugate
     double er = 1.0, ei = 0.0;
     for (int i = 0; i < m; ++i) {
       const double t = er * cp - ei * sp;
       ei = er * sp + ei * cp;
       er = t;
     }
+    w_m[lmax + m] = make_double2(er, -ei);
+    w_m[lmax - m] = make_double2(er, ei);
     double p_lm2 = 0.0, p_lm1 = pmm;
     for (int l = m; l <= lmax; ++l) {
-      double p;
-      if (l == m) p = pmm;
-      else if (l == m + 1) p = ct * (2.0 * m + 1.0) * pmm;
-      else p = ((2.0 * l - 1.0) * ct * p_lm1 - (l + m - 1.0) * p_lm2) / (double)(l - m);
+      double p = pmm;
       if (l > m) {
+        const int L = l * l + l + m;
+        p = kLeg.a[L] * (ct * p_lm1 - kLeg.b[L] * p_lm2);
         p_lm2 = p_lm1;
         p_lm1 = p;
       }
-      // N_lm = sqrt((2l + 1) / (4 pi) (l - m)! / (l + m)!)
-      double ratio = 1.0;
-      for (int i = l - m + 1; i <= l + m; ++i) ratio /= (double)i;
-      const double nrm = sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * ratio);
-      const double yr = nrm * p * er, yi = nrm * p * ei;  // Y_lm, m >= 0
-      // i^l conj(Y): conj(Y) = (yr, -yi); i^l rotates by l quarter turns
-      auto put = [&](int mm, double re, double im) {
-        double cr = re, ci = -im;  // conj
-        for (int q = 0; q < (l & 3); ++q) {
-          const double t = -ci;
-          ci = cr;
-          cr = t;
-        }
-        const int L = l * l + l + mm;
-        c_L[L] = make_double2(pref * cr, pref * ci);
-        l_of[L] = (unsigned char)l;
-      };
-      put(m, yr, yi);
-      if (m > 0) {  // Y_{l,-m} = (-1)^m conj(Y_lm)
-        const double sgn = (m & 1) ? -1.0 : 1.0;
-        put(-m, sgn * yr, -sgn * yi);
+      // i^l = (-1)^{floor(l/2)} i^{l mod 2}: the sign here, the factor i in the output
+      const double v = ((l & 2) ? -pref : pref) * p;
+      // conj(Y_lm) = Pbar_lm e^{-i m phi};  conj(Y_{l,-m}) = (-1)^m Y_lm = (-1)^m Pbar_lm e^{i m phi}
+      const int Lp = l * l + l + m, Lm = l * l + l - m;
+      P_L[Lp] = v;
+      l_of[Lp] = (unsigned char)l;
+      mi_of[Lp] = (unsigned char)(lmax + m);
+      if (m > 0) {
+        P_L[Lm] = (m & 1) ? -v : v;
+        l_of[Lm] = (unsigned char)l;
+        mi_of[Lm] = (unsigned char)(lmax - m);
       }
     }
   }
   __syncthreads();
 
-  // ---- per chunk of atoms: phases and radial factors, then the chunk's rows
+  // ---- per chunk of atoms: E and the radial factors, then the chunk's rows
+  const int step_i = kThreads / N_L, step_L = kThreads % N_L;
   for (int a0 = 0; a0 < N_A; a0 += kAtomChunk) {
     const int na = min(kAtomChunk, N_A - a0);
-    for (int i = threadIdx.x; i < na; i += blockDim.x) {
+    for (int i = threadIdx.x; i < na; i += kThreads) {
       const int a = a0 + i;
       double s, c;
       sincos(kx * tau[3 * a] + ky * tau[3 * a + 1] + kz * tau[3 * a + 2], &s, &c);
-      ph[i] = make_double2(c, s);
+      for (int k = 0; k < NM; ++k) {
+        const double2 w = w_m[k];
+        E[i][k] = make_double2(c * w.x - s * w.y, c * w.y + s * w.x);
+      }
       double j[kMaxL + 1], dj[kMaxL + 1];
       sph_bessel(Kn * R[a], lmax, j, dj);
       for (int l = 0; l <= lmax; ++l) {
         const double* uf = ufun + ((size_t)a * (lmax + 1) + l) * 4;
         const double u = uf[0], du = uf[1], ud = uf[2], dud = uf[3];
         const double rW = 1.0 / (u * dud - du * ud);  // 1 / Wronskian
-        fa[i][l] = (j[l] * dud - Kn * dj[l] * ud) * rW;
-        fb[i][l] = (Kn * dj[l] * u - j[l] * du) * rW;
+        const double kdj = Kn * dj[l];
+        fa[i][l] = (j[l] * dud - kdj * ud) * rW;
+        fb[i][l] = (kdj * u - j[l] * du) * rW;
       }
     }
     __syncthreads();
     double2* Ac = A + (size_t)g * ld + (size_t)a0 * N_L;
     double2* Bc = B + (size_t)g * ld + (size_t)a0 * N_L;
-    for (int r = threadIdx.x; r < na * N_L; r += blockDim.x) {
-      const int i = r / N_L, L = r - i * N_L;
-      const double2 p = ph[i], cl = c_L[L];
-      const double tr = p.x * cl.x - p.y * cl.y, ti = p.x * cl.y + p.y * cl.x;
+    const int nr = na * N_L;
+    int i = threadIdx.x / N_L, L = threadIdx.x % N_L;  // row r = i N_L + L
+    for (int r = threadIdx.x; r < nr; r += kThreads) {
+      const double2 e = E[i][mi_of[L]];
+      const double p = P_L[L];
       const int l = l_of[L];
-      Ac[r] = make_double2(tr * fa[i][l], ti * fa[i][l]);
-      Bc[r] = make_double2(tr * fb[i][l], ti * fb[i][l]);
+      double xr = e.x * p, xi = e.y * p;
+      if (l & 1) {  // times i
+        const double t = xr;
+        xr = -xi;
+        xi = t;
+      }
+      const double fA = fa[i][l], fB = fb[i][l];
+      Ac[r] = make_double2(xr * fA, xi * fA);
+      Bc[r] = make_double2(xr * fB, xi * fB);
+      i += step_i;
+      L += step_L;
+      if (L >= N_L) {
+        L -= N_L;
+        ++i;
+      }
     }
     __syncthreads();
   }

@@ -2,12 +2,12 @@
 FP64 oracle (``oracle/matching.py``), called through the C ABI.
 
 Tolerance: both sides compute in FP64.  The kernel's Y_lm come from the l recurrence
-of the Legendre functions, its j_l from Miller's downward recurrence normalised to
-j_0 or j_1, the oracle's from the power series of P_l and scipy; each product of the
-matching formula adds a few ulps.  An element may therefore differ by a small multiple
-of 1e-16 relative to itself plus the cancellation of the recurrences (bounded by the
-largest element of its column times ~1e-15); the test allows 1e-12 relative plus
-1e-13 of the matrix's largest element, a margin of ~100x.
+of the normalised Legendre functions, its j_l from Miller's downward recurrence
+normalised to j_0 or j_1; the oracle's from P_l differentiated in the Legendre basis,
+and scipy.  Each product of the matching formula adds a few ulps, so an element may
+differ by a small multiple of 1e-16 relative to itself plus the cancellation of the
+recurrences (bounded by the largest element of its column times ~1e-15); the test
+allows 1e-12 relative plus 1e-13 of the matrix's largest element, a margin of ~100x.
 """
 import math
 
