@@ -287,7 +287,10 @@ int hs_reduce_real(hs_plan_t plan, double* H, double* S, int N_G, hs_reduce_info
  *   [0, N_A N_L) of each column are written.
  * 0 <= l_max <= 11 (N_L <= 144); N_G = 0 returns HS_OK at once.  A zero W gives
  * non-finite coefficients (not checked).  stream is a cudaStream_t (NULL = legacy
- * default stream); the call returns after A and B are complete. */
+ * default stream); the call returns after A and B are complete.  It takes
+ * 48 N_A (l_max + 1) bytes of stream-ordered device scratch (cudaMallocAsync on that
+ * stream, freed before it returns) for the factors that do not depend on the plane
+ * wave; HS_ENOMEM if that allocation fails. */
 int hs_matching(const double* Kvec, const double* tau, const double* R, const double* ufun,
                 double omega, int N_A, int l_max, int N_G, hs_z* A, hs_z* B, int ld_AB,
                 void* stream);

@@ -80,29 +80,27 @@ constexpr LegendreTab make_legendre_tab() {
 
 __constant__ LegendreTab kLeg = make_legendre_tab();
 
-// j_l(x) for l = 0 .. lmax (x >= 0) and j_l'(x).  Miller's method: the recurrence
+// Unnormalised j_l(x), l = 0 .. lmax + 1, by Miller's method: the recurrence
 // f_{n-1} = (2n + 1) / x f_n - f_{n+1}, run downwards from
 // n0 = max(lmax + x + 6, x + 4.5 sqrt(x) + 6) (where j_n decays fast in n), is stable;
-// the sequence is rescaled when it nears overflow and normalised by whichever of
-// j_0 = sin x / x and j_1 = sin x / x^2 - cos x / x is larger in magnitude;
-// j_l' = (l / x) j_l - j_{l+1}.
-__device__ void sph_bessel(double x, int lmax, double* j, double* dj) {
-  if (x < 1e-30) {  // j_l(x) = x^l / (2l + 1)!! (1 + O(x^2)): below 1e-30 of j_0 for l > 0
-    for (int l = 0; l <= lmax; ++l) {
-      j[l] = l == 0 ? 1.0 : 0.0;
-      dj[l] = l == 1 ? 1.0 / 3.0 : 0.0;
-    }
-    return;
-  }
-  double f[kMaxL + 2];
+// the sequence is rescaled when it nears overflow.  Returns the factor that normalises
+// it, j_l = scale f_l, from whichever of j_0 = sin x / x and j_1 = sin x / x^2 - cos x / x
+// is larger in magnitude.  rx = 1 / x.  Below x = 1e-30, f = (1, 0, ...) and scale = 1:
+// j_l(x) = x^l / (2l + 1)!! (1 + O(x^2)) is below 1e-30 of j_0 there for l > 0.
+__device__ double miller(double x, double rx, int lmax, double* f) {
   for (int l = 0; l < kMaxL + 2; ++l) f[l] = 0.0;
+  if (x < 1e-30) {
+    f[0] = 1.0;
+    return 1.0;
+  }
   const int n0 = (int)fmax(lmax + x + 6.0, x + 4.5 * sqrt(x) + 6.0);
-  const double rx = 1.0 / x, rx2 = 2.0 * rx;
-  double coef = (2.0 * n0 + 1.0) * rx;  // (2n + 1) / x, stepped down by 2 / x
-  double fp1 = 0.0, fn = 1e-200;        // f_{n+1}, f_n
+  // 2n + 1 as an exact double counter; (2n + 1) * rx formed afresh each step (a
+  // coefficient stepped down by 2 / x drifts, and the drift costs ~1e-13 at x ~ 11)
+  double tn = 2.0 * n0 + 1.0;
+  double fp1 = 0.0, fn = 1e-200;  // f_{n+1}, f_n
   for (int n = n0; n >= 1; --n) {
-    const double fm1 = coef * fn - fp1;
-    coef -= rx2;
+    const double fm1 = tn * rx * fn - fp1;
+    tn -= 2.0;
     fp1 = fn;
     fn = fm1;
     // rescale when |f| passes 2^664 (exponent field of the high word: no FP64 compare)
@@ -116,27 +114,43 @@ __device__ void sph_bessel(double x, int lmax, double* j, double* dj) {
   double s, c;
   sincos(x, &s, &c);
   const double j0 = s * rx, j1 = (s * rx - c) * rx;
-  const double scale = fabs(j0) >= fabs(j1) ? j0 / f[0] : j1 / f[1];
-  for (int l = 0; l <= lmax + 1; ++l) f[l] *= scale;
-  for (int l = 0; l <= lmax; ++l) {
-    j[l] = f[l];
-    dj[l] = l * rx * f[l] - f[l + 1];
-  }
+  return fabs(j0) >= fabs(j1) ? j0 / f[0] : j1 / f[1];
+}
+
+// Per (atom, l) factors that do not depend on the plane wave, one thread each:
+//   rad = (udot'/W, udot/W, u/W, u'/W, l / R_a, 1 / R_a),   W = u udot' - u' udot.
+constexpr int kRad = 6;
+__global__ void k_matching_radial(const double* __restrict__ R, const double* __restrict__ ufun,
+                                  int N_A, int lmax, double* __restrict__ rad) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N_A * (lmax + 1)) return;
+  const int a = idx / (lmax + 1), l = idx - a * (lmax + 1);
+  const double u = ufun[4 * idx], du = ufun[4 * idx + 1], ud = ufun[4 * idx + 2],
+               dud = ufun[4 * idx + 3];
+  const double rW = 1.0 / (u * dud - du * ud);
+  const double rR = 1.0 / R[a];
+  double* o = rad + (size_t)idx * kRad;
+  o[0] = dud * rW;
+  o[1] = ud * rW;
+  o[2] = u * rW;
+  o[3] = du * rW;
+  o[4] = l * rR;
+  o[5] = rR;
 }
 
 __global__ void __launch_bounds__(kThreads) k_matching(const double* __restrict__ Kvec,
                                                        const double* __restrict__ tau,
                                                        const double* __restrict__ R,
-                                                       const double* __restrict__ ufun,
+                                                       const double* __restrict__ rad,
                                                        double pref, int N_A, int lmax, int N_G,
                                                        size_t ld, double2* __restrict__ A,
                                                        double2* __restrict__ B) {
   __shared__ double P_L[kMaxNL];                // (-1)^{floor(l/2)} pref sigma_m Pbar, real
   __shared__ unsigned char l_of[kMaxNL], mi_of[kMaxNL];
   __shared__ double2 w_m[kMaxM];                // e^{-i m phi} at index lmax + m
-  __shared__ double2 E[kAtomChunk][kMaxM];      // e^{i K.tau_a} e^{-i m phi}
-  __shared__ double fa[kAtomChunk][kMaxL + 1];  // radial factor of A (over W)
-  __shared__ double fb[kAtomChunk][kMaxL + 1];  // radial factor of B (over W)
+  __shared__ double2 E[kAtomChunk][kMaxM];      // scale_a e^{i K.tau_a} e^{-i m phi}
+  __shared__ double fa[kAtomChunk][kMaxL + 1];  // radial factor of A over scale_a
+  __shared__ double fb[kAtomChunk][kMaxL + 1];  // radial factor of B over scale_a
   const int g = blockIdx.x;
   if (g >= N_G) return;
   const int N_L = (lmax + 1) * (lmax + 1);
@@ -144,6 +158,7 @@ __global__ void __launch_bounds__(kThreads) k_matching(const double* __restrict_
   const double kx = Kvec[3 * g], ky = Kvec[3 * g + 1], kz = Kvec[3 * g + 2];
   const double rho = sqrt(kx * kx + ky * ky);
   const double Kn = sqrt(rho * rho + kz * kz);
+  const double rK = Kn > 0.0 ? 1.0 / Kn : 0.0;
   // direction of K; a zero vector (or one on the z axis) takes theta = 0 (phi = 0)
   const double ct = Kn > 0.0 ? kz / Kn : 1.0, st = Kn > 0.0 ? rho / Kn : 0.0;
   const double cp = rho > 0.0 ? kx / rho : 1.0, sp = rho > 0.0 ? ky / rho : 0.0;
@@ -194,21 +209,26 @@ __global__ void __launch_bounds__(kThreads) k_matching(const double* __restrict_
     const int na = min(kAtomChunk, N_A - a0);
     for (int i = threadIdx.x; i < na; i += kThreads) {
       const int a = a0 + i;
+      const double* rd = rad + (size_t)a * (lmax + 1) * kRad;
+      // radial part: j_l = scale f_l and, with K / x = 1 / R_a,
+      //   K j_l' = scale (l / R_a f_l - K f_{l+1}) = scale d_l;
+      //   f^A = scale (f_l udot' - d_l udot) / W,  f^B = scale (d_l u - f_l u') / W,
+      // the common factor scale moved into E
+      double f[kMaxL + 2];
+      const double scale = miller(Kn * R[a], rK * rd[5], lmax, f);
+      for (int l = 0; l <= lmax; ++l) {
+        const double* q = rd + l * kRad;
+        const double d = q[4] * f[l] - Kn * f[l + 1];
+        fa[i][l] = f[l] * q[0] - d * q[1];
+        fb[i][l] = d * q[2] - f[l] * q[3];
+      }
       double s, c;
       sincos(kx * tau[3 * a] + ky * tau[3 * a + 1] + kz * tau[3 * a + 2], &s, &c);
+      s *= scale;
+      c *= scale;
       for (int k = 0; k < NM; ++k) {
         const double2 w = w_m[k];
         E[i][k] = make_double2(c * w.x - s * w.y, c * w.y + s * w.x);
-      }
-      double j[kMaxL + 1], dj[kMaxL + 1];
-      sph_bessel(Kn * R[a], lmax, j, dj);
-      for (int l = 0; l <= lmax; ++l) {
-        const double* uf = ufun + ((size_t)a * (lmax + 1) + l) * 4;
-        const double u = uf[0], du = uf[1], ud = uf[2], dud = uf[3];
-        const double rW = 1.0 / (u * dud - du * ud);  // 1 / Wronskian
-        const double kdj = Kn * dj[l];
-        fa[i][l] = (j[l] * dud - kdj * ud) * rW;
-        fb[i][l] = (kdj * u - j[l] * du) * rW;
       }
     }
     __syncthreads();
@@ -252,9 +272,18 @@ extern "C" int hs_matching(const double* Kvec, const double* tau, const double* 
   if (N_G == 0) return HS_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const double pref = 4.0 * M_PI / sqrt(omega);
-  k_matching<<<N_G, kThreads, 0, st>>>(Kvec, tau, R, ufun, pref, N_A, l_max, N_G,
+  const int nrad = N_A * (l_max + 1);
+  double* rad = nullptr;
+  if (cudaMallocAsync((void**)&rad, sizeof(double) * kRad * nrad, st) != cudaSuccess) {
+    cudaGetLastError();
+    return HS_ENOMEM;
+  }
+  k_matching_radial<<<(nrad + 255) / 256, 256, 0, st>>>(R, ufun, N_A, l_max, rad);
+  k_matching<<<N_G, kThreads, 0, st>>>(Kvec, tau, R, rad, pref, N_A, l_max, N_G,
                                        (size_t)ld_AB, (double2*)A, (double2*)B);
-  HS_CUDA_TRY(cudaGetLastError());
+  const cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(rad, st);
+  HS_CUDA_TRY(e);
   HS_CUDA_TRY(cudaStreamSynchronize(st));
   return HS_OK;
 }
