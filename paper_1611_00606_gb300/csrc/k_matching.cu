@@ -11,19 +11,23 @@
 // GB300 runs FP64 at 2 operations per clock per SM, so this kernel is bound by its
 // FP64 arithmetic, not by the stores of A and B; it is arranged to spend as few FP64
 // operations per output element as the formula allows.  With conj(Y_lm) written as
-// N_l|m| P_l^|m|(cos theta) e^{-i m phi} (times (-1)^m for m < 0), each element is the
-// product of three factors, two of them real:
-//   A_{aL} = [e^{i K.tau_a} e^{-i m phi}] * [i^l pref sigma N P]_L * f^A_{al},
-// the complex one per (atom, m), the real one per row L, the radial one per (atom, l)
-// and shared with B (f^B in place of f^A): 2 products for X = E * P_L, the factor i^l
-// applied as a sign and a swap, then 2 products each for A and B.
+// Pbar_l|m|(cos theta) e^{-i m phi} (times (-1)^m for m < 0), each element is the
+// product of three factors:
+//   A_{aL} = [scale_a e^{i K.tau_a} e^{-i m phi}] * i^l [pref sigma Pbar]_L * f^A_{al},
+// a complex one per (atom, m), a real one per row L and a real radial one per
+// (atom, l), shared with B (f^B in place of f^A).  The factor i^l is a sign, kept in
+// the row table P2, and a swap of the real and imaginary parts of E, so an element
+// costs 2 FP64 products for X = i^l E P_L and 2 each for A and B, with no additions
+// and no negations.
 //
-// One CTA per plane wave g, all atoms: the per-row factors P_L and e^{-i m phi} in
-// shared memory (normalised associated Legendre functions by their l recurrence with
-// compile-time coefficients, Condon-Shortley phase), then per chunk of atoms one thread per atom computes
-// E_{a,m} and the radial factors (j_l for all l by Miller's downward recurrence,
-// normalised to j_0 or j_1), then the column's rows of the chunk, contiguous in the
-// column-major layout, are written by consecutive threads.
+// A pre-pass kernel computes the factors that do not depend on the plane wave (the
+// radial boundary values over the Wronskian W, l / R_a).  Then one CTA per plane
+// wave g, all atoms: the per-row factors P2_L and e^{-i m phi} in shared memory
+// (normalised associated Legendre functions by their l recurrence with compile-time
+// coefficients, Condon-Shortley phase); per chunk of atoms, one thread per atom
+// computes E_{a,m} and the radial factors (j_l for all l by Miller's downward
+// recurrence), then consecutive threads write the chunk's rows of the column, which
+// are contiguous in the column-major layout.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -145,7 +149,8 @@ __global__ void __launch_bounds__(kThreads) k_matching(const double* __restrict_
                                                        double pref, int N_A, int lmax, int N_G,
                                                        size_t ld, double2* __restrict__ A,
                                                        double2* __restrict__ B) {
-  __shared__ double P_L[kMaxNL];                // (-1)^{floor(l/2)} pref sigma_m Pbar, real
+  __shared__ double2 P2[kMaxNL];                // (v, v) for even l, (-v, v) for odd l,
+                                                // v = (-1)^{floor(l/2)} pref sigma_m Pbar
   __shared__ unsigned char l_of[kMaxNL], mi_of[kMaxNL];
   __shared__ double2 w_m[kMaxM];                // e^{-i m phi} at index lmax + m
   __shared__ double2 E[kAtomChunk][kMaxM];      // scale_a e^{i K.tau_a} e^{-i m phi}
@@ -191,11 +196,12 @@ __global__ void __launch_bounds__(kThreads) k_matching(const double* __restrict_
       const double v = ((l & 2) ? -pref : pref) * p;
       // conj(Y_lm) = Pbar_lm e^{-i m phi};  conj(Y_{l,-m}) = (-1)^m Y_lm = (-1)^m Pbar_lm e^{i m phi}
       const int Lp = l * l + l + m, Lm = l * l + l - m;
-      P_L[Lp] = v;
+      P2[Lp] = make_double2((l & 1) ? -v : v, v);
       l_of[Lp] = (unsigned char)l;
       mi_of[Lp] = (unsigned char)(lmax + m);
       if (m > 0) {
-        P_L[Lm] = (m & 1) ? -v : v;
+        const double vm = (m & 1) ? -v : v;
+        P2[Lm] = make_double2((l & 1) ? -vm : vm, vm);
         l_of[Lm] = (unsigned char)l;
         mi_of[Lm] = (unsigned char)(lmax - m);
       }
@@ -238,14 +244,11 @@ __global__ void __launch_bounds__(kThreads) k_matching(const double* __restrict_
     int i = threadIdx.x / N_L, L = threadIdx.x % N_L;  // row r = i N_L + L
     for (int r = threadIdx.x; r < nr; r += kThreads) {
       const double2 e = E[i][mi_of[L]];
-      const double p = P_L[L];
+      const double2 p = P2[L];
       const int l = l_of[L];
-      double xr = e.x * p, xi = e.y * p;
-      if (l & 1) {  // times i
-        const double t = xr;
-        xr = -xi;
-        xi = t;
-      }
+      // times i for odd l: (e.x, e.y) p -> (-e.y p, e.x p), the sign taken from P2
+      const bool odd = l & 1;
+      const double xr = (odd ? e.y : e.x) * p.x, xi = (odd ? e.x : e.y) * p.y;
       const double fA = fa[i][l], fB = fb[i][l];
       Ac[r] = make_double2(xr * fA, xi * fA);
       Bc[r] = make_double2(xr * fB, xi * fB);
