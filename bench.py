@@ -762,14 +762,18 @@ def run_main(args, w):
         hT = [[pin(t) for t in T], [pin(t) for t in T]]  # two copies: re-factor each step
         hH = torch.empty((w.N_G, w.N_G), dtype=torch.complex128, pin_memory=True).T
         hS = torch.empty((w.N_G, w.N_G), dtype=torch.complex128, pin_memory=True).T
-        e_steps = args.e2e_steps or max(2, args.steps // 4)
+        e_steps = args.e2e_steps or max(4, args.steps // 2)
         for i in range(2):
             hs.hs_assemble_host(plan, hA, hB, *hT[i % 2], hU, w.N_A, w.N_L, w.N_G, hH, hS)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        calls = []
         for i in range(e_steps):
-            hs.hs_assemble_host(plan, hA, hB, *hT[i % 2], hU, w.N_A, w.N_L, w.N_G, hH, hS)
+            tc = time.perf_counter()
+            inf_e = hs.hs_assemble_host(plan, hA, hB, *hT[i % 2], hU, w.N_A, w.N_L, w.N_G,
+                                        hH, hS)
+            calls.append((1e3 * (time.perf_counter() - tc), inf_e["ms_total"]))
         torch.cuda.synchronize()
         t_e = time.perf_counter() - t0
         t_e = reduce_max(t_e, dev)
@@ -777,6 +781,7 @@ def run_main(args, w):
         e2e = {"value": F * ws * e_steps / t_e / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 2 * 16 * w.N_G * w.N_G, "steps": e_steps,
                "kpts_per_s": ws * e_steps / t_e, "ms_per_step": 1e3 * t_e / e_steps,
+               "calls_ms": [{"wall": round(a, 1), "device": round(b, 1)} for a, b in calls],
                "call": "hs_assemble_host (pinned host buffers; copies of A, B, T, U in and "
                        "H, S out inside the timed region)"}
         del hA, hB, hU, hT, hH, hS
@@ -963,7 +968,8 @@ def main():
     ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp64"])
     ap.add_argument("--slices", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=1, help="steps of the FP64 form (0: skip)")
-    ap.add_argument("--e2e-steps", type=int, default=0, help="hs_assemble_host steps (0: steps/4)")
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="hs_assemble_host steps (0: max(4, steps/2))")
     ap.add_argument("--ref-cols", type=int, default=0,
                     help="oracle panel width per step of --impl reference (0: by workload)")
     ap.add_argument("--cpu-cols", type=int, default=0,
