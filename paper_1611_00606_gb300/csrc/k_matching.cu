@@ -161,12 +161,24 @@ __global__ void __launch_bounds__(kThreads) k_matching(const double* __restrict_
   const int N_L = (lmax + 1) * (lmax + 1);
   const int NM = 2 * lmax + 1;
   const double kx = Kvec[3 * g], ky = Kvec[3 * g + 1], kz = Kvec[3 * g + 2];
-  const double rho = sqrt(kx * kx + ky * ky);
-  const double Kn = sqrt(rho * rho + kz * kz);
-  const double rK = Kn > 0.0 ? 1.0 / Kn : 0.0;
-  // direction of K; a zero vector (or one on the z axis) takes theta = 0 (phi = 0)
-  const double ct = Kn > 0.0 ? kz / Kn : 1.0, st = Kn > 0.0 ? rho / Kn : 0.0;
-  const double cp = rho > 0.0 ? kx / rho : 1.0, sp = rho > 0.0 ? ky / rho : 0.0;
+  // |K|, 1/|K| and the direction of K, computed once per column by one thread (the
+  // square roots and divisions cost tens of FP64 operations, which every thread of the
+  // CTA repeating them would multiply by 256); a zero vector (or one on the z axis)
+  // takes theta = 0 (phi = 0)
+  __shared__ double col[6];  // |K|, 1/|K|, cos theta, sin theta, cos phi, sin phi
+  if (threadIdx.x == 0) {
+    const double rho = sqrt(kx * kx + ky * ky);
+    const double kn = sqrt(rho * rho + kz * kz);
+    col[0] = kn;
+    col[1] = kn > 0.0 ? 1.0 / kn : 0.0;
+    col[2] = kn > 0.0 ? kz / kn : 1.0;
+    col[3] = kn > 0.0 ? rho / kn : 0.0;
+    col[4] = rho > 0.0 ? kx / rho : 1.0;
+    col[5] = rho > 0.0 ? ky / rho : 0.0;
+  }
+  __syncthreads();
+  const double Kn = col[0], rK = col[1];
+  const double ct = col[2], st = col[3], cp = col[4], sp = col[5];
 
   // ---- per-row factors: thread m runs the l recurrence of order m
   if (threadIdx.x <= lmax) {
