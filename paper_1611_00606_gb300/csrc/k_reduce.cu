@@ -21,7 +21,7 @@
 namespace {
 
 constexpr int NB = 64;   // diagonal block of the Cholesky and of the inverse
-constexpr int RT = 64;   // output tile of k_zgemm (rows and columns)
+constexpr int kNumSMs = 152;  // GB300
 constexpr int RK = 16;   // K step of k_zgemm
 constexpr int kThreads = 256;
 
@@ -216,36 +216,43 @@ struct ZgemmArgs {
   const int* fail;
 };
 
+// TS x TS output tiles (TS = 64 or 32), 256 threads with (TS/16) x (TS/16) complex
+// results each.  GB300 runs FP64 at 2 operations per clock per SM, so a tile's time is
+// its FP64 work on one SM: skinny products (the updates inside a Cholesky panel, a
+// few dozen 64-wide tiles) take the 32-wide tiles, which spread the same work over
+// four times as many SMs.
+template <int TS>
 __global__ void __launch_bounds__(kThreads, 2) k_zgemm(const ZgemmArgs g) {
-  __shared__ double2 As[RK][RT];
-  __shared__ double2 Bs[RK][RT + 1];
+  constexpr int RP = TS / 16;  // results per thread along rows and along columns
+  __shared__ double2 As[RK][TS];
+  __shared__ double2 Bs[RK][TS + 1];
   if (*g.fail) return;
   const int ti = gridDim.y - 1 - blockIdx.y, tj = gridDim.x - 1 - blockIdx.x;
   if (g.lower && tj > ti) return;
-  const int r0 = ti * RT, c0 = tj * RT;
+  const int r0 = ti * TS, c0 = tj * TS;
   int kb = 0, ke = g.k;
-  if (g.triA) ke = min(ke, r0 + RT);
-  if (g.triB) ke = min(ke, c0 + RT);
+  if (g.triA) ke = min(ke, r0 + TS);
+  if (g.triB) ke = min(ke, c0 + TS);
   if (g.halfB) kb = c0;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double2 acc[4][4];
+  double2 acc[RP][RP];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RP; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+    for (int j = 0; j < RP; ++j) acc[i][j] = make_double2(0.0, 0.0);
 
   for (int k0 = kb; k0 < ke; k0 += RK) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < RP; ++q) {  // RK x TS = 256 RP elements per operand
       const int e = tid + kThreads * q;
-      {  // A: 64 rows x 16 k, consecutive threads on consecutive rows
-        const int rr = e & 63, kk = e >> 6;
+      {  // A: TS rows x 16 k, consecutive threads on consecutive rows
+        const int rr = e % TS, kk = e / TS;
         const int r = r0 + rr, kx = k0 + kk;
         As[kk][rr] = (r < g.m && kx < ke) ? g.A[(size_t)r + (size_t)kx * g.lda]
                                           : make_double2(0.0, 0.0);
       }
       if (g.conjB) {  // op(B)[k][c] = conj(B[c + k ldb]): consecutive threads on c
-        const int cc = e & 63, kk = e >> 6;
+        const int cc = e % TS, kk = e / TS;
         const int c = c0 + cc, kx = k0 + kk;
         Bs[kk][cc] = (c < g.n && kx < ke) ? zconj(g.B[(size_t)c + (size_t)kx * g.ldb])
                                           : make_double2(0.0, 0.0);
@@ -264,22 +271,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_zgemm(const ZgemmArgs g) {
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < RK; ++kk) {
-      double2 a[4], b[4];
+      double2 a[RP], b[RP];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < RP; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < RP; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RP; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) zfma(acc[i][j], a[i], b[j]);
+        for (int j = 0; j < RP; ++j) zfma(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RP; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < RP; ++j) {
       const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * j;
       if (r < g.m && c < g.n) {
         double2* p = g.C + (size_t)r + (size_t)c * g.ldc;
@@ -385,10 +392,21 @@ __global__ void k_sub(double2* __restrict__ C, int ldc, const double2* __restric
   }
 }
 
+// 64-wide tiles unless that leaves most SMs idle: fewer than two 64-wide tiles per SM
+// take 32-wide tiles.  The choice depends on m and n only, never on the structure
+// flags: P = W tril_h(H) writes only tiles on or below the diagonal and
+// G = P W^H (triA) reads P up to the end of each tile's rows, so both products of one
+// n must tile alike.
 cudaError_t zgemm(const ZgemmArgs& g, cudaStream_t st) {
   if (g.m <= 0 || g.n <= 0) return cudaSuccess;
-  const dim3 grid((g.n + RT - 1) / RT, (g.m + RT - 1) / RT);
-  k_zgemm<<<grid, kThreads, 0, st>>>(g);
+  const long long t64 = (long long)((g.n + 63) / 64) * ((g.m + 63) / 64);
+  if (t64 < 2 * kNumSMs) {
+    const dim3 grid((g.n + 31) / 32, (g.m + 31) / 32);
+    k_zgemm<32><<<grid, kThreads, 0, st>>>(g);
+  } else {
+    const dim3 grid((g.n + 63) / 64, (g.m + 63) / 64);
+    k_zgemm<64><<<grid, kThreads, 0, st>>>(g);
+  }
   return cudaGetLastError();
 }
 

@@ -87,6 +87,8 @@ def _check(C, L, H, S, precision="fp64"):
     (130, 1e4),      # three tiles, ragged
     (257, 1e3),      # five tiles, 1-wide tail; several Cholesky panels
     (520, 1e6),      # nine panels, ragged, ill-conditioned
+    (1000, 1e4),     # 32-wide tiles of the FP64 products (fewer than 2 x 152 64-wide)
+    (1300, 1e3),     # 64-wide tiles for the two-sided products, 32-wide late in the Cholesky
 ])
 def test_reduce_parity(hs, n, cond):
     H, S = synth.reduce_inputs(n, seed=n + 7, cond=cond)
