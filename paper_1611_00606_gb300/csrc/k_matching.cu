@@ -26,8 +26,9 @@
 // (normalised associated Legendre functions by their l recurrence with compile-time
 // coefficients, Condon-Shortley phase); per chunk of atoms, one thread per atom
 // computes E_{a,m} and the radial factors (j_l for all l by Miller's downward
-// recurrence), then consecutive threads write the chunk's rows of the column, which
-// are contiguous in the column-major layout.
+// recurrence, or upwards when |K| R_a exceeds l_max + 8), then consecutive threads
+// write the chunk's rows of the column, which are contiguous in the column-major
+// layout.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -84,17 +85,28 @@ constexpr LegendreTab make_legendre_tab() {
 
 __constant__ LegendreTab kLeg = make_legendre_tab();
 
-// Unnormalised j_l(x), l = 0 .. lmax + 1, by Miller's method: the recurrence
-// f_{n-1} = (2n + 1) / x f_n - f_{n+1}, run downwards from
-// n0 = max(lmax + x + 6, x + 4.5 sqrt(x) + 6) (where j_n decays fast in n), is stable;
-// the sequence is rescaled when it nears overflow.  Returns the factor that normalises
-// it, j_l = scale f_l, from whichever of j_0 = sin x / x and j_1 = sin x / x^2 - cos x / x
-// is larger in magnitude.  rx = 1 / x.  Below x = 1e-30, f = (1, 0, ...) and scale = 1:
-// j_l(x) = x^l / (2l + 1)!! (1 + O(x^2)) is below 1e-30 of j_0 there for l > 0.
+// Unnormalised j_l(x), l = 0 .. lmax + 1, and the factor that normalises them,
+// j_l = scale f_l; rx = 1 / x.  The recurrence f_{n-1} + f_{n+1} = (2n + 1) / x f_n
+// of the spherical Bessel functions is run
+// * upwards from j_0 = sin x / x and j_1 = sin x / x^2 - cos x / x when x > lmax + 8:
+//   every order needed is below x, where the upward direction is stable (scale = 1);
+// * otherwise downwards (Miller's method) from n0 = max(lmax + x + 6, x + 4.5 sqrt(x) + 6),
+//   where j_n decays fast in n, rescaled when it nears overflow, and normalised by
+//   whichever of j_0, j_1 is larger in magnitude.
+// Below x = 1e-30, f = (1, 0, ...) and scale = 1: j_l(x) = x^l / (2l + 1)!! (1 + O(x^2))
+// is below 1e-30 of j_0 there for l > 0.
 __device__ double miller(double x, double rx, int lmax, double* f) {
   for (int l = 0; l < kMaxL + 2; ++l) f[l] = 0.0;
   if (x < 1e-30) {
     f[0] = 1.0;
+    return 1.0;
+  }
+  if (x > lmax + 8.0) {
+    double s, c;
+    sincos(x, &s, &c);
+    f[0] = s * rx;
+    f[1] = (s * rx - c) * rx;
+    for (int l = 1; l <= lmax; ++l) f[l + 1] = (2.0 * l + 1.0) * rx * f[l] - f[l - 1];
     return 1.0;
   }
   const int n0 = (int)fmax(lmax + x + 6.0, x + 4.5 * sqrt(x) + 6.0);

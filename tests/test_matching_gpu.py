@@ -72,8 +72,9 @@ def test_matching_parity(hs, N_A, l_max, N_G, seed):
 
 def test_matching_special_directions(hs):
     """K = 0 (Y_00 only), K along +z and -z (sin theta = 0, phi undefined: 0), K in
-    the xy plane, and one wave vector long enough that x = |K| R exceeds l_max (the
-    Bessel recurrence starts above x there)."""
+    the xy plane, one wave vector long enough that x = |K| R exceeds l_max + 8 (the
+    Bessel recurrence runs upwards there) and one just below that switch (Miller's
+    recurrence started above x)."""
     d = synth.matching_inputs(4, 6, 40, seed=7)
     K = d["Kvec"].copy()
     K[0] = 0.0
@@ -82,6 +83,7 @@ def test_matching_special_directions(hs):
     K[3] = (0.9, -0.4, 0.0)
     K[4] = (7.0, -11.0, 5.0)     # |K| R ~ 30
     K[5] = (1e-3, 0.0, 0.0)      # small x: j_l ~ x^l / (2l + 1)!!
+    K[6] = (0.0, 13.0 / d["R"][0], 0.0)  # x = 13 for atom 0 (<= l_max + 8 = 14), 9.5-18 for the others
     d = dict(d, Kvec=K)
     A, B = _check(hs, d, 6)
     N_L = 49
