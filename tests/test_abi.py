@@ -62,3 +62,25 @@ def test_strerror_and_argument_validation(lib):
     lib.hs_footprint.restype = C.c_size_t
     assert lib.hs_footprint(None, 10) == 0
     assert lib.hs_destroy(None) == -1
+
+
+def test_matching_argument_validation(lib):
+    """hs_matching rejects bad arguments before any device call (host-side checks)."""
+    from paper_1611_00606_gb300 import hs
+    restype, argtypes = hs.SIGNATURES["hs_matching"]
+    f = lib.hs_matching
+    f.restype, f.argtypes = restype, argtypes
+    p = C.c_void_p(16)   # stand-in addresses: never dereferenced on these paths
+    q = C.c_void_p(32)
+
+    def call(K=p, tau=p, R=p, u=p, omega=1.0, N_A=2, l_max=3, N_G=8, A=p, B=q, ld=32):
+        return f(K, tau, R, u, omega, N_A, l_max, N_G, A, B, ld, None)
+
+    assert call(K=None) == -1 and call(tau=None) == -1 and call(R=None) == -1
+    assert call(u=None) == -1 and call(A=None) == -1 and call(B=None) == -1
+    assert call(B=p) == -1                       # A and B the same buffer
+    assert call(N_A=0) == -1 and call(l_max=-1) == -1 and call(l_max=12) == -1
+    assert call(N_G=-1) == -1
+    assert call(omega=0.0) == -1 and call(omega=-2.0) == -1 and call(omega=float("nan")) == -1
+    assert call(ld=31) == -1                     # below N_A (l_max + 1)^2 = 32
+    assert call(N_G=0) == 0                      # nothing to do, nothing touched
