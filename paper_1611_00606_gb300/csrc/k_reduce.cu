@@ -71,12 +71,13 @@ __global__ void __launch_bounds__(kThreads) k_potrf_diag(double2* __restrict__ S
       if (tid == 0) atomicCAS(fail, 0, j0 + k + 1);
       return;
     }
-    // one thread takes the square root and the reciprocal (FP64 issues slowly on this
-    // GPU: every warp repeating them cost as much as the column's update)
+    // one thread takes 1/sqrt (FP64 issues slowly on this GPU: every warp repeating it
+    // cost as much as the column's update); L_kk = d / sqrt(d)
     double l = 0.0;
     if (tid == 0) {
-      l = sqrt(d);
-      s_rl = 1.0 / l;
+      const double rl = rsqrt(d);
+      l = d * rl;
+      s_rl = rl;
     }
     __syncthreads();  // every thread has read d: the diagonal may now hold L_kk
     if (tid == 0) a[k * NB + k] = make_double2(l, 0.0);
@@ -86,11 +87,24 @@ __global__ void __launch_bounds__(kThreads) k_potrf_diag(double2* __restrict__ S
       a[k * NB + r].y *= rl;
     }
     __syncthreads();
-    // trailing lower triangle: 16 x 16 threads over (row, column) pairs
-    const int tx = tid & 15, ty = tid >> 4;
-    for (int c = k + 1 + ty; c < jb; c += 16) {
-      const double2 lc = a[k * NB + c];
-      for (int r = c + tx; r < jb; r += 16) zfms_conj(a[c * NB + r], a[k * NB + r], lc);
+    // trailing lower triangle, m columns: column k + 1 + p (m - p entries) is paired with
+    // column jb - 1 - p (p + 1 entries), so every pair holds m + 1 entries and the
+    // ceil(m / 2) x (m + 1) pairs spread evenly over the threads (consecutive threads on
+    // consecutive rows of one column)
+    const int m = jb - k - 1;
+    const int np = (m + 1) / 2;
+    for (int e = tid; e < np * (m + 1); e += kThreads) {
+      const int p = e / (m + 1), q = e - p * (m + 1);
+      int c, r;
+      if (q < m - p) {
+        c = k + 1 + p;
+        r = c + q;
+      } else {
+        c = jb - 1 - p;
+        r = c + (q - (m - p));
+        if (c == k + 1 + p) continue;  // odd m: the middle column pairs with itself
+      }
+      zfms_conj(a[c * NB + r], a[k * NB + r], a[k * NB + c]);
     }
   }
   __syncthreads();
@@ -127,10 +141,14 @@ __global__ void __launch_bounds__(kSmallThreads) k_trsm_rpanel(double2* __restri
     x[e] = (r < nr && c < jb) ? S[(size_t)(rb + r) + (size_t)(j0 + c) * ld]
                               : make_double2(0.0, 0.0);
   }
+  // the diagonal's reciprocals up front, in parallel, off the column chain
+  __shared__ double rdiag[NB];
+  for (int c = tid; c < jb; c += kSmallThreads)
+    rdiag[c] = 1.0 / S[(size_t)(j0 + c) + (size_t)(j0 + c) * ld].x;
   for (int c = 0; c < jb; ++c) {
     __syncthreads();
     if (tid < RPR) {
-      const double rl = 1.0 / Lb[c * NB + c].x;
+      const double rl = rdiag[c];
       x[c * RPR + tid].x *= rl;
       x[c * RPR + tid].y *= rl;
     }
@@ -174,10 +192,14 @@ __global__ void __launch_bounds__(kSmallThreads) k_trsm_ldiag(const double2* __r
     x[r * XS + col] = (r < ib && col < nc) ? X[(size_t)(i0 + r) + (size_t)(c0 + col) * ldx]
                                            : make_double2(0.0, 0.0);
   }
+  // the diagonal's reciprocals up front, in parallel, off the row chain
+  __shared__ double rdiag[NB];
+  for (int k = tid; k < ib; k += kSmallThreads)
+    rdiag[k] = 1.0 / L[(size_t)(i0 + k) + (size_t)(i0 + k) * ldl].x;
   for (int k = 0; k < ib; ++k) {
     __syncthreads();
     if (tid < RPR) {
-      const double rl = 1.0 / Lb[k * NB + k].x;
+      const double rl = rdiag[k];
       x[k * XS + tid].x *= rl;
       x[k * XS + tid].y *= rl;
     }
