@@ -767,6 +767,8 @@ def run_main(args, w):
             hs.hs_assemble_host(plan, hA, hB, *hT[i % 2], hU, w.N_A, w.N_L, w.N_G, hH, hS)
         barrier()
         torch.cuda.synchronize()
+        clk_e = ClockSampler(torch.cuda.current_device())
+        clk_e.start()
         t0 = time.perf_counter()
         calls = []
         for i in range(e_steps):
@@ -776,12 +778,14 @@ def run_main(args, w):
             calls.append((1e3 * (time.perf_counter() - tc), inf_e["ms_total"]))
         torch.cuda.synchronize()
         t_e = time.perf_counter() - t0
+        clocks_e = clk_e.stop()
         t_e = reduce_max(t_e, dev)
         h2d = 16 * K * w.N_G * 2 + 8 * K + 3 * 16 * w.N_A * w.N_L * w.N_L
         e2e = {"value": F * ws * e_steps / t_e / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 2 * 16 * w.N_G * w.N_G, "steps": e_steps,
                "kpts_per_s": ws * e_steps / t_e, "ms_per_step": 1e3 * t_e / e_steps,
                "calls_ms": [{"wall": round(a, 1), "device": round(b, 1)} for a, b in calls],
+               "clocks": clocks_e,
                "call": "hs_assemble_host (pinned host buffers; copies of A, B, T, U in and "
                        "H, S out inside the timed region)"}
         del hA, hB, hU, hT, hH, hS
