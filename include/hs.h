@@ -259,10 +259,12 @@ typedef struct {
 } hs_reduce_info;
 int hs_reduce(hs_plan_t plan, hs_z* H, hs_z* S, int N_G, hs_reduce_info* info);
 /* The same for the real-symmetric variant: real symmetric H and S (DEVICE pointers,
- * N_G x N_G column-major, leading dimension N_G) on a plan made with HS_FP64 | HS_REAL;
+ * N_G x N_G column-major, leading dimension N_G) on a plan made with HS_REAL;
  * S <- L (real), H <- C (real symmetric).  The pair is embedded as complex and reduced
- * by the FP64 kernels (imaginary parts stay exactly zero).  Split real plans:
- * HS_ENOTSUP; complex plans: HS_EINVAL.  HS_ENOTPD leaves H and S unchanged. */
+ * by the plan's form (FP64 plans: the FP64 kernels; split plans: the split form's,
+ * with its error bound), imaginary parts staying exactly zero; split real plans
+ * allocate the two complex N_G_max x N_G_max buffers of the embedding on first use.
+ * Complex plans: HS_EINVAL.  HS_ENOTPD leaves H and S unchanged. */
 int hs_reduce_real(hs_plan_t plan, double* H, double* S, int N_G, hs_reduce_info* info);
 
 /* ---------------------------------------------------------------------------

@@ -739,11 +739,19 @@ extern "C" int hs_reduce(hs_plan_t p, hs_z* H, hs_z* S, int N_G, hs_reduce_info*
 extern "C" int hs_reduce_real(hs_plan_t p, double* H, double* S, int N_G, hs_reduce_info* info) {
   if (info) std::memset(info, 0, sizeof(*info));
   if (!p || !H || !S || N_G < 0 || N_G > p->N_G_max || !p->real) return HS_EINVAL;
-  if (p->precision != HS_FP64) return HS_ENOTSUP;
   if (N_G == 0) return HS_OK;
   if (H == S) return HS_EINVAL;
   std::lock_guard<std::mutex> lk(p->mu);
-  if (!p->Hc || !p->Sc) return HS_ENOTSUP;
+  if (!p->Hc || !p->Sc) {  // split real plans: the complex embedding on first use
+    const size_t bytes = (size_t)16 * p->N_G_max * p->N_G_max;
+    if ((!p->Hc && cudaMalloc((void**)&p->Hc, bytes) != cudaSuccess) ||
+        (!p->Sc && cudaMalloc((void**)&p->Sc, bytes) != cudaSuccess)) {
+      cudaGetLastError();
+      free_ptr((void*&)p->Hc);
+      free_ptr((void*&)p->Sc);
+      return HS_ENOMEM;
+    }
+  }
   cudaStream_t st = p->stream;
   for (auto& e : p->real_ev)
     if (!e) HS_CUDA_TRY(cudaEventCreate(&e));

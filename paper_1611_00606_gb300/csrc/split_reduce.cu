@@ -95,7 +95,7 @@ static int contract_tiles(const SplitParams& P) {
 
 int hs_plan_s::split_reduce_transform(const double2* B, double2* H, int n, cudaStream_t st,
                                       cudaEvent_t mid) {
-  if (precision != HS_SPLIT_BF16 || real || n < 1) return HS_EINVAL;
+  if (precision != HS_SPLIT_BF16 || n < 1) return HS_EINVAL;  // real plans: complex embedding
   int rc = split_reduce_alloc(n);
   if (rc) return rc;
   const int s = slices;

@@ -239,9 +239,35 @@ def test_reduce_real_fp64(hs):
             hs.hs_reduce_real(p.h, Hd, Sd)
     assert e.value.code == hs.HS_ENOTPD and e.value.fail_col == reduce_standard(Hr, Sbad)[2]
     assert np.array_equal(Hd.cpu().numpy(), Hr) and np.array_equal(Sd.cpu().numpy(), Sbad)
-    # split real plans are not supported, complex plans take hs_reduce
-    for prec, code in (("split_bf16_real", hs.HS_ENOTSUP), ("fp64", hs.HS_EINVAL)):
-        with hs.Plan(1, 1, n, prec) as p:
-            with pytest.raises(hs.HSError) as e:
-                hs.hs_reduce_real(p.h, Hd, Sd)
-            assert e.value.code == code
+    # complex plans take hs_reduce
+    with hs.Plan(1, 1, n, "fp64") as p:
+        with pytest.raises(hs.HSError) as e:
+            hs.hs_reduce_real(p.h, Hd, Sd)
+        assert e.value.code == hs.HS_EINVAL
+
+
+@pytest.mark.parametrize("n", [200, 777])
+def test_reduce_real_split(hs, n):
+    """hs_reduce_real on a split real plan (the pair embedded as complex, the split
+    form's kernels): L and C within the split form's bound of the oracle, L lower with a
+    zero upper triangle, C exactly symmetric; a failing pivot leaves both unchanged."""
+    H, S = synth.reduce_inputs(n, seed=22 + n, cond=1e3)
+    Hr, Sr = np.asfortranarray(H.real), np.asfortranarray(S.real)
+    Hd, Sd = hs.to_device_real(Hr), hs.to_device_real(Sr)
+    with hs.Plan(1, 1, n, "split_bf16_real") as p:
+        info = hs.hs_reduce_real(p.h, Hd, Sd)
+    C, L = Hd.cpu().numpy(), Sd.cpu().numpy()
+    Lr, Cr, fail = reduce_standard(Hr, Sr)
+    assert fail == 0 and info["fail_col"] == 0
+    tol = _tol(Sr, "split_bf16")
+    assert np.all(np.triu(L, 1) == 0)
+    assert rel_frobenius(L, Lr.real) <= tol and rel_frobenius(C, Cr.real) <= tol
+    assert np.array_equal(C, C.T)
+    Sbad = Sr.copy()
+    Sbad[40, 40] = -1.0
+    Hd, Sd = hs.to_device_real(Hr), hs.to_device_real(Sbad)
+    with hs.Plan(1, 1, n, "split_bf16_real") as p:
+        with pytest.raises(hs.HSError) as e:
+            hs.hs_reduce_real(p.h, Hd, Sd)
+    assert e.value.code == hs.HS_ENOTPD and e.value.fail_col == reduce_standard(Hr, Sbad)[2]
+    assert np.array_equal(Hd.cpu().numpy(), Hr) and np.array_equal(Sd.cpu().numpy(), Sbad)
