@@ -128,13 +128,27 @@ __device__ __forceinline__ void tc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uin
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
-  uint32_t r[4];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(taddr));
+// W = 8 or 16 consecutive TMEM columns of this warp's 32 lanes, one register each.
+template <int W>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[W]) {
+  static_assert(W == 8 || W == 16, "8 or 16 columns");
+  uint32_t r[W];
+  if constexpr (W == 8) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+  } else {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+  }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < W; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -210,26 +224,47 @@ __device__ __forceinline__ void fast_two_sum_acc2(f32x2& hi, f32x2& lo, f32x2 v)
 // 2^(E_row + E_col): the window sums of levels 0-2 are exact integers and go into
 // hi (TwoSum for levels 0 and 1, Fast2Sum for level 2, read after them); levels
 // >= 3 go into lo.
-template <int S, uint32_t MASK>
-__device__ __forceinline__ void drain16(uint32_t taddr, f32x2 (&hi)[8], f32x2 (&lo)[8]) {
+//
+// drain_cols reads W columns of every accumulator in MASK with one load-and-wait
+// round trip and folds them into pairs k0 .. k0 + W/2 - 1.  Every round trip waits
+// out the TMEM load latency, so drain16 takes the widest reads the 96-register budget
+// holds: the common window (levels 2 and >= 3 due) in one round trip of 16 columns,
+// three accumulators in two of 8, and all four in four of 8 (levels 0 and 1, then 2
+// and >= 3, so that every element still sees levels 0, 1, 2, 3 in that order and the
+// result is unchanged).
+template <int S, uint32_t MASK, int W>
+__device__ __forceinline__ void drain_cols(uint32_t taddr, int k0, f32x2 (&hi)[8],
+                                           f32x2 (&lo)[8]) {
   constexpr bool r0 = MASK & 1u, r1 = MASK & 2u, r2 = S >= 3 && (MASK & 4u),
                  r3 = S >= 4 && (MASK & 8u);
+  float v0[W], v1[W], v2[W], v3[W];
+  if (r0) tmem_ld<W>(taddr, v0);
+  if (r1) tmem_ld<W>(taddr + BN, v1);
+  if (r2) tmem_ld<W>(taddr + 2 * BN, v2);
+  if (r3) tmem_ld<W>(taddr + 3 * BN, v3);
+  tmem_wait_ld();
 #pragma unroll
-  for (int c0 = 0; c0 < 16; c0 += 4) {
-    float v0[4], v1[4], v2[4], v3[4];
-    if (r0) tmem_ld4(taddr + c0, v0);
-    if (r1) tmem_ld4(taddr + BN + c0, v1);
-    if (r2) tmem_ld4(taddr + 2 * BN + c0, v2);
-    if (r3) tmem_ld4(taddr + 3 * BN + c0, v3);
-    tmem_wait_ld();
+  for (int c = 0; c < W; c += 2) {
+    const int k = k0 + (c >> 1);
+    if (r0) two_sum_acc2(hi[k], lo[k], pack2(v0[c], v0[c + 1]));
+    if (r1) two_sum_acc2(hi[k], lo[k], pack2(v1[c], v1[c + 1]));
+    if (r2) fast_two_sum_acc2(hi[k], lo[k], pack2(v2[c], v2[c + 1]));
+    if (r3) lo[k] = add2(lo[k], pack2(v3[c], v3[c + 1]));
+  }
+}
+template <int S, uint32_t MASK>
+__device__ __forceinline__ void drain16(uint32_t taddr, f32x2 (&hi)[8], f32x2 (&lo)[8]) {
+  if constexpr (MASK == 0xCu) {
+    drain_cols<S, MASK, 16>(taddr, 0, hi, lo);
+  } else if constexpr (S >= 4 && MASK == 0xFu) {
 #pragma unroll
-    for (int c = 0; c < 4; c += 2) {
-      const int k = (c0 + c) >> 1;
-      if (r0) two_sum_acc2(hi[k], lo[k], pack2(v0[c], v0[c + 1]));
-      if (r1) two_sum_acc2(hi[k], lo[k], pack2(v1[c], v1[c + 1]));
-      if (r2) fast_two_sum_acc2(hi[k], lo[k], pack2(v2[c], v2[c + 1]));
-      if (r3) lo[k] = add2(lo[k], pack2(v3[c], v3[c + 1]));
+    for (int c0 = 0; c0 < 16; c0 += 8) {
+      drain_cols<S, 0x3u, 8>(taddr + c0, c0 >> 1, hi, lo);
+      drain_cols<S, 0xCu, 8>(taddr + c0, c0 >> 1, hi, lo);
     }
+  } else {
+#pragma unroll
+    for (int c0 = 0; c0 < 16; c0 += 8) drain_cols<S, MASK, 8>(taddr + c0, c0 >> 1, hi, lo);
   }
 }
 
@@ -636,17 +671,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
           ++nwin;
         }
       }
-      if (!ok || *abort_flag) break;
+      if (!is_contract(MODE) && (!ok || *abort_flag)) break;
       // Results: (hi + lo) * 2^(E_row + E_col) in FP64.  Thread = one tile row; pair k
       // of a strip = its TMEM columns 16 cg + 2k and 2k + 1 (lanes 2k, 2k + 1 of eC*).
       if (is_contract(MODE)) {
         // one tile per CTA: stage (hi, lo) in the idle ring (every stage was consumed by
         // an MMA that completed before the last acc_full), then write the tile with
-        // consecutive threads on consecutive output addresses
+        // consecutive threads on consecutive output addresses.  Every drain warp reaches
+        // the staging barrier exactly once, also after a failed wait (the launch then
+        // reports an error and stores nothing): warps that leave here on their own view
+        // of the abort flag would otherwise leave the others at the barrier.
         float2* stg = (float2*)smem;  // [2 strips][64 cols][128 rows]
         int* s_erow = (int*)(smem + 2 * 64 * 128 * sizeof(float2));
         int* s_ecol = s_erow + 128;   // [128]: exponent of each TMEM column
         const int r = 32 * q4 + lane;
+        const bool good = ok && !*abort_flag;
+        if (good)
 #pragma unroll
         for (int c = 0; c < 16; c += 2) {
           const float2 ha = unpack2(h0[c >> 1]), la = unpack2(l0[c >> 1]);
@@ -663,7 +703,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) k_split_gemm(const __grid_cons
         }
         asm volatile("bar.sync 1, %0;" ::"r"(32 * NUM_DRAIN_WARPS) : "memory");
         const int dt = threadIdx.x - 64;  // 0 .. 32*NUM_DRAIN_WARPS-1
-        if (is_real(MODE)) {  // 128 real columns
+        if (!good) {
+        } else if (is_real(MODE)) {  // 128 real columns
           double* C = (double*)P.C;
           for (int idx = dt; idx < 128 * 128; idx += 32 * NUM_DRAIN_WARPS) {
             const int jj = idx >> 7, ii = idx & 127;
